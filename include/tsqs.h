@@ -1,0 +1,230 @@
+/*
+ * tsqs.h -- C-ABI of the GB300-native three-way partition sort (Triple State
+ * QuickSort, Muqaddas, arXiv 1505.00558).
+ *
+ * The library replaces qsort() for fixed key kinds (the paper's stated goal, abstract
+ * and Section VII): a comparator pointer becomes a key kind, the element size must
+ * match that kind, and the sort runs on one CUDA device (sm_103a) as
+ *   pivot kernel      a sampled median per segment        (Section III.H, V.C)
+ *   partition kernel  <p | =p | >p split of every segment (Section III.A-F)
+ *   work queue        device-built segment frontier that replaces recursion (Fig. 1)
+ *   leaf kernel       on-chip sort of segments of <= small_threshold elements and
+ *                     the fill of every =p run                  (Section IV, III.F)
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* / base are DEVICE pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The library owns its scratch (see
+ *     tsqs_free_storage) and never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).  Calls
+ *     are asynchronous on that stream unless stated otherwise.
+ *   - Sorting is ascending under a total order on whole elements (integers numeric,
+ *     floats IEEE 754 totalOrder, records (key, payload)).  Equal elements are
+ *     bitwise identical, so the sorted output is unique and deterministic.
+ *   - Return value: TSQS_OK or a tsqs_status code.  Nothing is thrown across the ABI.
+ *     Argument errors are reported before any work is queued.  Errors raised on the
+ *     device (a bounded wait that expired, an internal inconsistency) are sticky in the
+ *     context and reported by tsqs_last_device_status(); after such an error the
+ *     contents of the array are unspecified.
+ *   - Limits: nmemb < 2^31 per segment (partition counters are 31-bit fields); base must
+ *     be aligned to elem_size (16 bytes for records).
+ */
+#ifndef TSQS_H
+#define TSQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Key kinds (replace the paper's cmp callback, Section III / VII). */
+typedef enum {
+    TSQS_I32 = 1,          /* int32,  elem_size 4                                   */
+    TSQS_U32 = 2,          /* uint32, elem_size 4                                   */
+    TSQS_F32 = 3,          /* float32 under IEEE totalOrder, elem_size 4            */
+    TSQS_I64 = 4,          /* int64,  elem_size 8                                   */
+    TSQS_U64 = 5,          /* uint64, elem_size 8                                   */
+    TSQS_F64 = 6,          /* float64 under IEEE totalOrder, elem_size 8            */
+    TSQS_U64_U64_REC = 7   /* {uint64 key; uint64 payload}, ordered by (key, payload),
+                              elem_size 16                                          */
+} tsqs_key_kind;
+
+typedef enum {
+    TSQS_OK = 0,
+    TSQS_EINVAL = 1,       /* bad argument (null pointer, size mismatch, alignment)  */
+    TSQS_ENOMEM = 2,       /* device scratch could not be allocated / over budget    */
+    TSQS_ECUDA = 3,        /* a CUDA runtime call failed                             */
+    TSQS_ETIMEOUT = 4,     /* a bounded device-side wait expired                     */
+    TSQS_EINTERNAL = 5     /* device-side consistency check failed                   */
+} tsqs_status;
+
+/* Tunables of one sort (the plan the autotuner picks).  Zero fields take defaults. */
+typedef struct {
+    int32_t  tile_items;       /* keys per thread in a partition tile (4-byte keys: 8/16) */
+    int32_t  small_threshold;  /* segments of <= this many elements finish on chip (<= 4096) */
+    int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
+    int32_t  sample_count;     /* pivot sample size: 15, 31 or 63                      */
+    uint64_t seed;             /* seed of the jittered sample positions (Section V.C)   */
+} tsqs_plan;
+
+/* Per-context statistics of the last completed sort (filled by tsqs_ctx_stats). */
+typedef struct {
+    uint32_t levels;           /* partition levels run                                  */
+    uint32_t max_frontier;     /* most segments in one level                            */
+    uint64_t partition_keys;   /* keys read by all partition levels                     */
+    uint64_t leaf_sorted_keys; /* keys finished by the on-chip sorter                   */
+    uint64_t leaf_filled_keys; /* keys written by =p fills                              */
+    uint64_t leaf_items;       /* leaf work items processed                             */
+    uint32_t level_keys_count; /* entries used in level_keys                            */
+    uint32_t pad;
+    uint64_t level_keys[64];   /* keys partitioned at level i (first 64 levels)         */
+} tsqs_stats;
+
+typedef struct tsqs_ctx tsqs_ctx;   /* scratch + captured graphs of one independent sorter */
+
+/* ---------------------------------------------------------------------------------
+ * Core sort (Section III-IV: the qsort replacement, one segment).
+ *   base       device array of nmemb elements of elem_size bytes, sorted in place.
+ *   key_kind   tsqs_key_kind; elem_size must equal its size.
+ *   nmemb <= 1 returns TSQS_OK with no launch.
+ * Uses the library's default context; calls from several streams are serialised on
+ * its scratch by events.
+ * ------------------------------------------------------------------------------- */
+int tsqs_sort(void *base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
+
+/* Segmented sort: sorts every segment [d_seg_offsets[s], d_seg_offsets[s+1]) of base
+ * independently, all in one launch sequence.  d_seg_offsets is a DEVICE array of
+ * nseg+1 non-decreasing uint64 offsets with d_seg_offsets[nseg] <= total capacity of
+ * base; nmemb_total must equal d_seg_offsets[nseg] (used to size scratch). */
+int tsqs_sort_segmented(void *base, size_t nmemb_total, const uint64_t *d_seg_offsets,
+                        size_t nseg, size_t elem_size, int key_kind, void *stream);
+
+/* Host-memory convenience (the paper's qsort(): array in host memory).  Copies h_base
+ * to library-owned device memory, sorts, copies back, and synchronises `stream`
+ * before returning.  h_base should be pinned for full copy bandwidth. */
+int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
+
+/* Frees the default context's device scratch (Section III.G:
+ * FreeTripleStateQuickSortStorage).  Synchronises the device first. */
+void tsqs_free_storage(void);
+
+/* Synchronises `stream` and returns the default context's sticky device status
+ * (TSQS_OK, TSQS_ETIMEOUT or TSQS_EINTERNAL), then clears it. */
+int tsqs_last_device_status(void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Explicit contexts: independent scratch and graphs, e.g. one per stream.
+ * ------------------------------------------------------------------------------- */
+tsqs_ctx *tsqs_ctx_create(const tsqs_plan *plan);          /* NULL plan = defaults */
+void tsqs_ctx_destroy(tsqs_ctx *ctx);                      /* synchronises first  */
+int tsqs_ctx_sort(tsqs_ctx *ctx, void *base, size_t nmemb, size_t elem_size, int key_kind,
+                  void *stream);
+int tsqs_ctx_sort_segmented(tsqs_ctx *ctx, void *base, size_t nmemb_total,
+                            const uint64_t *d_seg_offsets, size_t nseg, size_t elem_size,
+                            int key_kind, void *stream);
+/* Reserves scratch for sorts up to (nmemb_total, nseg) of elem_size so that later calls
+ * allocate nothing (and may run under stream capture). */
+int tsqs_ctx_reserve(tsqs_ctx *ctx, size_t nmemb_total, size_t nseg, size_t elem_size);
+size_t tsqs_ctx_scratch_bytes(const tsqs_ctx *ctx);
+int tsqs_ctx_device_status(tsqs_ctx *ctx, void *stream);   /* sync + read + clear */
+int tsqs_ctx_stats(tsqs_ctx *ctx, void *stream, tsqs_stats *out);   /* sync + read */
+int tsqs_ctx_set_plan(tsqs_ctx *ctx, const tsqs_plan *plan);
+int tsqs_ctx_get_plan(const tsqs_ctx *ctx, tsqs_plan *out);
+
+/* Bytes of device scratch a context needs for a sort of this shape. */
+size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
+                              const tsqs_plan *plan);
+
+/* Default plan for a key kind and size (autotuned values when a tuning table was
+ * loaded with tsqs_plan_load, built-in defaults otherwise). */
+int tsqs_plan_default(int key_kind, size_t n_hint, tsqs_plan *out);
+
+/* ---------------------------------------------------------------------------------
+ * Instrumented level-by-level run (for measurement): the same kernels launched one at
+ * a time from the host, with a CUDA event recorded around every partition launch.
+ * Synchronises `stream`.  Writes up to max_levels partition-kernel durations (ms) to
+ * h_ms and the keys each of those launches read to h_keys; returns the number of
+ * levels through *levels.
+ * ------------------------------------------------------------------------------- */
+int tsqs_ctx_sort_timed(tsqs_ctx *ctx, void *base, size_t nmemb, size_t elem_size,
+                        int key_kind, void *stream, float *h_ms, uint64_t *h_keys,
+                        int max_levels, int *levels, float *h_leaf_ms);
+
+/* ---------------------------------------------------------------------------------
+ * Step-level entry points (used to test each kernel alone against the oracle).
+ * ------------------------------------------------------------------------------- */
+
+/* Pivot kernel on one segment [seg_begin, seg_end) of base: writes the sample
+ * positions it used (sample_count uint64, host) and the pivot element (elem_size
+ * bytes, host, original representation).  Synchronises `stream`. */
+int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_kind,
+                     uint64_t seg_begin, uint64_t seg_end, int sample_count, uint64_t seed,
+                     uint64_t *h_positions, void *h_pivot, void *stream);
+
+/* One partition level: for every segment s of d_seg_offsets (device, nseg+1) with pivot
+ * d_pivots[s] (device, original representation, elem_size bytes each), reads src and
+ * writes dst over the same range: the elements < p packed from the left, the elements
+ * > p packed from the right; the =p run in between is not written.  Writes
+ * d_counts[2*s] = #<p and d_counts[2*s+1] = #>p (device uint64).  src and dst must
+ * not overlap.  Synchronises `stream`. */
+int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_size,
+                         int key_kind, const uint64_t *d_seg_offsets, size_t nseg,
+                         const void *d_pivots, uint64_t *d_counts, void *stream);
+
+/* Leaf kernel alone: sorts every segment of d_seg_offsets (each must hold at most
+ * small_threshold elements of the default plan) in place.  Synchronises `stream`. */
+int tsqs_debug_small_sort(void *base, size_t nmemb, size_t elem_size, int key_kind,
+                          const uint64_t *d_seg_offsets, size_t nseg, void *stream);
+
+/* Forces the bounded look-back wait of the next partition level of the default
+ * context to give up after `polls` polls (0 restores the default).  Used by tests
+ * to check that an expired wait surfaces as TSQS_ETIMEOUT. */
+void tsqs_debug_set_spin_limit(uint32_t polls);
+
+/* When on != 0, partition tile 1 of every later level of the default context never
+ * publishes its look-back word, so the waits of its successors must run into the
+ * spin limit and the sort must end with TSQS_ETIMEOUT (a host-side fault injection
+ * that neither faults nor hangs the device).  0 restores normal operation. */
+void tsqs_debug_withhold_publish(int on);
+
+/* ---------------------------------------------------------------------------------
+ * Batching: one captured CUDA graph per (context, key kind) replayed for every call;
+ * tsqs_plan_autotune times candidate plans on a synthetic batch and returns the best.
+ * ------------------------------------------------------------------------------- */
+int tsqs_plan_autotune(int key_kind, size_t n_hint, size_t nseg_hint, void *stream,
+                       tsqs_plan *out);
+
+/* ---------------------------------------------------------------------------------
+ * Serving: continuous batching of sort requests that arrive over time.
+ * ------------------------------------------------------------------------------- */
+typedef struct tsqs_server tsqs_server;
+
+typedef struct {
+    int32_t  status;        /* tsqs_status of the request (TSQS_OK when sorted)        */
+    int32_t  done;          /* 1 once the result is complete on the device             */
+    double   t_submit;      /* host seconds (monotonic) when tsqs_server_submit ran   */
+    double   t_start;       /* host seconds when the request was launched              */
+    double   t_done;        /* host seconds when its completion was observed           */
+    uint32_t batch_id;      /* launch that carried it                                  */
+    uint32_t batch_size;    /* requests in that launch                                 */
+} tsqs_result;
+
+/* mem_budget_bytes bounds the device scratch plus in-flight request bytes;
+ * n_streams launches may be in flight at once; max_batch bounds requests per launch. */
+tsqs_server *tsqs_server_create(size_t mem_budget_bytes, int n_streams, int max_batch);
+/* Queues a request on d_base (device, caller-owned, must stay valid until done).
+ * Returns TSQS_ENOMEM if the request alone can never fit the budget. */
+int tsqs_server_submit(tsqs_server *s, void *d_base, size_t nmemb, size_t elem_size,
+                       int key_kind, uint64_t *ticket);
+/* Admits queued requests that fit, launches batches, retires finished ones.  Call it
+ * from the host loop; returns the number of requests still pending or in flight. */
+int tsqs_server_progress(tsqs_server *s);
+int tsqs_server_poll(tsqs_server *s, uint64_t ticket, tsqs_result *out);
+int tsqs_server_drain(tsqs_server *s);          /* progress until nothing is pending */
+void tsqs_server_destroy(tsqs_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSQS_H */

@@ -1,0 +1,702 @@
+// tsqs_host.cu -- host runtime and C-ABI of the three-way partition sort.
+//
+// A context owns one block of device scratch (the second buffer of the ping-pong,
+// the work queues and the look-back words; the analogue of the persistent temporary
+// storage of Section III.G) and one CUDA graph per key kind.  The graph is
+//     init  ->  while (queues not empty) { leaf ; pivot ; partition ; finish }
+// with the loop condition set on the device by the finish kernel, so a whole sort is
+// one graph launch with no host round trip between levels.  Every kernel reads the
+// per-call description (Job) from device memory, written by a one-thread setup kernel
+// launched just before the graph, so the same graph serves every array of its kind.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "tsqs.h"
+#include "tsqs_internal.h"
+
+using namespace tsqs;
+
+namespace tsqs {
+__global__ void k_setup(Job *job, Ctl *ctl, Job j);
+}
+
+namespace {
+
+constexpr uint32_t kDefaultSpin = 1u << 22;     // look-back polls before giving up
+
+const KindOps *get_ops(int kind) {
+    if (kind >= TSQS_I32 && kind <= TSQS_F32) return ops_k4(kind);
+    if (kind >= TSQS_I64 && kind <= TSQS_F64) return ops_k8(kind);
+    if (kind == TSQS_U64_U64_REC) return ops_k16(kind);
+    return nullptr;
+}
+
+size_t kind_size(int kind) {
+    const KindOps *o = get_ops(kind);
+    return o ? (size_t)o->elem_size : 0;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t alt_off, front_off[2], leaves_off[2], tseg_off, tstat_off, done_off, misc_off, total;
+    uint32_t cap_front, cap_tiles, cap_leaves;
+};
+
+// Scratch needed for nmemb elements in nseg segments (bounds, not estimates):
+//   frontier  segments above small_T in one level are disjoint: <= n/(T+1) (+ nseg for
+//             the step-level partition test, which seeds every given segment)
+//   tiles     <= n/TILE + 2 per segment (partial first and last tiles)
+//   leaves    <= 2 children per partitioned segment, n/kFillChunk + 1 fill items per
+//             segment, plus the small root segments
+Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int tile) {
+    Layout L{};
+    const size_t T = (size_t)plan.small_threshold;
+    const size_t cf = n / (T + 1) + nseg + 4;
+    const size_t ct = n / (size_t)tile + 2 * cf + 4;
+    const size_t cl = 3 * cf + n / kFillChunk + nseg + 4;
+    L.cap_front = (uint32_t)std::min<size_t>(cf, 0xFFFFFFF0u);
+    L.cap_tiles = (uint32_t)std::min<size_t>(ct, 0xFFFFFFF0u);
+    L.cap_leaves = (uint32_t)std::min<size_t>(cl, 0xFFFFFFF0u);
+    size_t off = 0;
+    L.alt_off = off;            off = align_up(off + n * es + 16, 256);
+    L.front_off[0] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
+    L.front_off[1] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
+    L.leaves_off[0] = off;      off = align_up(off + cl * sizeof(LeafItem), 256);
+    L.leaves_off[1] = off;      off = align_up(off + cl * sizeof(LeafItem), 256);
+    L.tseg_off = off;           off = align_up(off + ct * sizeof(uint32_t), 256);
+    L.tstat_off = off;          off = align_up(off + ct * sizeof(unsigned long long), 256);
+    L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
+    L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
+    L.total = off;
+    return L;
+}
+
+void fill_default_plan(int key_kind, size_t, tsqs_plan *p) {
+    (void)key_kind;
+    p->tile_items = 0;            // fixed per key size in this build
+    p->small_threshold = kMaxSmall;
+    p->ctas_per_sm = 0;           // occupancy-derived
+    p->sample_count = 31;
+    p->seed = 0x5EED5EED12345678ull;
+}
+
+void normalise_plan(tsqs_plan *p) {
+    tsqs_plan d;
+    fill_default_plan(TSQS_I32, 0, &d);
+    if (p->small_threshold <= 0) p->small_threshold = d.small_threshold;
+    if (p->small_threshold > kMaxSmall) p->small_threshold = kMaxSmall;
+    if (p->small_threshold < 64) p->small_threshold = 64;
+    if (p->sample_count <= 0) p->sample_count = d.sample_count;
+    if (p->sample_count > kMaxSamples) p->sample_count = kMaxSamples;
+    if ((p->sample_count & 1) == 0) p->sample_count -= 1;
+    if (p->seed == 0) p->seed = d.seed;
+    if (p->ctas_per_sm < 0) p->ctas_per_sm = 0;
+}
+
+uint32_t g_debug_spin = 0;        // 0 = default
+int g_debug_withhold = 0;
+
+}  // namespace
+
+struct tsqs_ctx {
+    tsqs_plan plan{};
+    int device = -1;
+    int sms = 0;
+    Job *d_job = nullptr;
+    Ctl *d_ctl = nullptr;
+    char *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaGraph_t graph[8] = {};
+    cudaGraphExec_t exec[8] = {};
+    int part_grid[8] = {}, leaf_grid[8] = {};
+    bool attrs_set[8] = {};
+    cudaEvent_t done_ev = nullptr;
+    bool ev_valid = false;
+    unsigned int *h_cont = nullptr;    // pinned word for the host-driven loop
+    std::recursive_mutex mu;
+};
+
+namespace {
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            if (getenv("TSQS_VERBOSE"))                                                  \
+                fprintf(stderr, "tsqs: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+            return TSQS_ECUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+int ctx_init_device(tsqs_ctx *c) {
+    if (c->device >= 0) return TSQS_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaMalloc((void **)&c->d_job, sizeof(Job)));
+    CK(cudaMalloc((void **)&c->d_ctl, sizeof(Ctl)));
+    CK(cudaMemset(c->d_ctl, 0, sizeof(Ctl)));
+    CK(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming));
+    CK(cudaHostAlloc((void **)&c->h_cont, sizeof(unsigned int), cudaHostAllocDefault));
+    c->device = dev;
+    return TSQS_OK;
+}
+
+int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
+    const int k = o->kind;
+    if (c->attrs_set[k]) return TSQS_OK;
+    CK(cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem));
+    int occ_p = 0, occ_l = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, o->k_partition, o->part_block, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem));
+    if (c->plan.ctas_per_sm > 0) occ_p = std::min(occ_p, c->plan.ctas_per_sm);
+    c->part_grid[k] = std::max(1, occ_p) * c->sms;
+    c->leaf_grid[k] = std::max(1, occ_l) * c->sms;
+    c->attrs_set[k] = true;
+    return TSQS_OK;
+}
+
+// Waits for all work that may still use the scratch (every stream that sorted with it).
+int ctx_quiesce(tsqs_ctx *c) {
+    if (c->ev_valid) CK(cudaEventSynchronize(c->done_ev));
+    return TSQS_OK;
+}
+
+int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile) {
+    const Layout L = make_layout(n, nseg, es, c->plan, tile);
+    if (c->scratch && L.total <= c->scratch_bytes) return TSQS_OK;
+    int rc = ctx_quiesce(c);
+    if (rc) return rc;
+    if (c->scratch) { cudaFree(c->scratch); c->scratch = nullptr; c->scratch_bytes = 0; }
+    const size_t want = L.total + L.total / 8;          // headroom against regrowth
+    if (cudaMalloc((void **)&c->scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc((void **)&c->scratch, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            c->scratch = nullptr;
+            return TSQS_ENOMEM;
+        }
+        c->scratch_bytes = L.total;
+    } else {
+        c->scratch_bytes = want;
+    }
+    return TSQS_OK;
+}
+
+// Fills the per-call description.  The scratch buffer gets the same 16-byte phase as
+// base so that both buffers use the same tile geometry.
+int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t *offs,
+             size_t nseg, Job *j) {
+    const size_t es = (size_t)o->elem_size;
+    const Layout L = make_layout(n, nseg, es, c->plan, o->tile);
+    if (L.total > c->scratch_bytes) return TSQS_EINTERNAL;
+    memset(j, 0, sizeof(*j));
+    const uintptr_t b = (uintptr_t)base;
+    j->base = base;
+    j->alt = c->scratch + L.alt_off + (b & 15u);
+    j->n = n;
+    j->seg_offsets = offs;
+    j->nseg = offs ? nseg : 1;
+    j->front[0] = (SegDesc *)(c->scratch + L.front_off[0]);
+    j->front[1] = (SegDesc *)(c->scratch + L.front_off[1]);
+    j->leaves[0] = (LeafItem *)(c->scratch + L.leaves_off[0]);
+    j->leaves[1] = (LeafItem *)(c->scratch + L.leaves_off[1]);
+    j->tile_seg = (uint32_t *)(c->scratch + L.tseg_off);
+    j->tile_status = (unsigned long long *)(c->scratch + L.tstat_off);
+    j->seg_done = (uint32_t *)(c->scratch + L.done_off);
+    j->cap_front = L.cap_front;
+    j->cap_tiles = L.cap_tiles;
+    j->cap_leaves = L.cap_leaves;
+    j->small_T = (uint32_t)c->plan.small_threshold;
+    j->samples = (uint32_t)c->plan.sample_count;
+    j->vec_off = (uint32_t)((b / es) % (16 / es));
+    j->spin_limit = g_debug_spin ? g_debug_spin : kDefaultSpin;
+    j->pad = g_debug_withhold ? 2u : 0u;
+    // depth cap: far above what sampled medians need (about log2(n / T) + a few)
+    unsigned lg = 1;
+    while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
+    j->max_levels = 256u + 8u * lg;
+    j->seed = c->plan.seed;
+    return TSQS_OK;
+}
+
+int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
+    const int k = o->kind;
+    if (c->exec[k]) return TSQS_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)o->k_init;
+    kp.gridDim = dim3(c->sms * 2);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args2;
+    cudaGraphNode_t n_init;
+    CK(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp));
+
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_loop;
+    CK(cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    cudaGraphNode_t n_leaf, n_piv, n_part, n_fin;
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_leaf;
+    kp.gridDim = dim3(c->leaf_grid[k]);
+    kp.blockDim = dim3(o->leaf_block);
+    kp.sharedMemBytes = (unsigned)o->leaf_smem;
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_leaf, body, nullptr, 0, &kp));
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_pivot;
+    kp.gridDim = dim3(c->sms * 4);
+    kp.blockDim = dim3(o->pivot_block);
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_piv, body, &n_leaf, 1, &kp));
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_partition;
+    kp.gridDim = dim3(c->part_grid[k]);
+    kp.blockDim = dim3(o->part_block);
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_part, body, &n_piv, 1, &kp));
+    int use_h = 1;
+    unsigned int unused = 0;
+    void *argsf[] = {&pj, &pc, &h, &use_h, &unused};
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_finish;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = argsf;
+    CK(cudaGraphAddKernelNode(&n_fin, body, &n_part, 1, &kp));
+
+    cudaGraphExec_t ex = nullptr;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    c->graph[k] = g;
+    c->exec[k] = ex;
+    return TSQS_OK;
+}
+
+int validate(void *base, size_t nmemb, size_t elem_size, int key_kind) {
+    const size_t es = kind_size(key_kind);
+    if (!es || es != elem_size) return TSQS_EINVAL;
+    if (nmemb > 1 && !base) return TSQS_EINVAL;
+    const size_t align = es == 16 ? 16 : es;
+    if ((uintptr_t)base % align) return TSQS_EINVAL;
+    return TSQS_OK;
+}
+
+// Queues one sort (single segment when offs == nullptr).
+int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t nseg,
+               size_t elem_size, int key_kind, cudaStream_t stream) {
+    int rc = validate(base, n, elem_size, key_kind);
+    if (rc) return rc;
+    if (!offs && n >= (1ull << 31)) return TSQS_EINVAL;
+    if (offs && nseg == 0) return TSQS_OK;
+    if (!offs && n <= 1) return TSQS_OK;
+    if (offs && n == 0) return TSQS_OK;
+    const KindOps *o = get_ops(key_kind);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if ((rc = ctx_init_device(c))) return rc;
+    if ((rc = ctx_kind_setup(c, o))) return rc;
+    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, o->tile))) return rc;
+    if ((rc = ctx_build_graph(c, o))) return rc;
+    Job j;
+    if ((rc = make_job(c, o, base, n, offs, nseg, &j))) return rc;
+    if (c->ev_valid) CK(cudaStreamWaitEvent(stream, c->done_ev, 0));
+    k_setup<<<1, 256, 0, stream>>>(c->d_job, c->d_ctl, j);
+    CK(cudaGetLastError());
+    CK(cudaGraphLaunch(c->exec[key_kind], stream));
+    CK(cudaEventRecord(c->done_ev, stream));
+    c->ev_valid = true;
+    return TSQS_OK;
+}
+
+std::mutex g_default_mu;
+tsqs_ctx *g_default = nullptr;
+
+tsqs_ctx *default_ctx() {
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (!g_default) g_default = tsqs_ctx_create(nullptr);
+    return g_default;
+}
+
+int read_status(tsqs_ctx *c, cudaStream_t stream, bool clear) {
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if (c->device < 0) return TSQS_OK;
+    CK(cudaStreamSynchronize(stream));
+    if (c->ev_valid) CK(cudaEventSynchronize(c->done_ev));
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, &c->d_ctl->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (clear && st) CK(cudaMemset(&c->d_ctl->status, 0, sizeof(uint32_t)));
+    return (int)st;
+}
+
+}  // namespace
+
+// =================================================================================
+// C-ABI
+// =================================================================================
+
+extern "C" {
+
+tsqs_ctx *tsqs_ctx_create(const tsqs_plan *plan) {
+    tsqs_ctx *c = new (std::nothrow) tsqs_ctx();
+    if (!c) return nullptr;
+    if (plan) c->plan = *plan;
+    else fill_default_plan(TSQS_I32, 0, &c->plan);
+    normalise_plan(&c->plan);
+    return c;
+}
+
+void tsqs_ctx_destroy(tsqs_ctx *c) {
+    if (!c) return;
+    {
+        std::lock_guard<std::recursive_mutex> lk(c->mu);
+        ctx_quiesce(c);
+        for (int k = 0; k < 8; k++) {
+            if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+            if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+        }
+        if (c->scratch) cudaFree(c->scratch);
+        if (c->d_job) cudaFree(c->d_job);
+        if (c->d_ctl) cudaFree(c->d_ctl);
+        if (c->done_ev) cudaEventDestroy(c->done_ev);
+        if (c->h_cont) cudaFreeHost(c->h_cont);
+    }
+    delete c;
+}
+
+int tsqs_ctx_set_plan(tsqs_ctx *c, const tsqs_plan *plan) {
+    if (!c || !plan) return TSQS_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int rc = ctx_quiesce(c);
+    if (rc) return rc;
+    c->plan = *plan;
+    normalise_plan(&c->plan);
+    for (int k = 0; k < 8; k++) {            // grids depend on the plan
+        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+        c->exec[k] = nullptr;
+        c->graph[k] = nullptr;
+        c->attrs_set[k] = false;
+    }
+    return TSQS_OK;
+}
+
+int tsqs_ctx_get_plan(const tsqs_ctx *c, tsqs_plan *out) {
+    if (!c || !out) return TSQS_EINVAL;
+    *out = c->plan;
+    return TSQS_OK;
+}
+
+int tsqs_ctx_sort(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size, int key_kind,
+                  void *stream) {
+    if (!c) return TSQS_EINVAL;
+    return ctx_launch(c, base, nmemb, nullptr, 0, elem_size, key_kind, (cudaStream_t)stream);
+}
+
+int tsqs_ctx_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
+                            const uint64_t *d_seg_offsets, size_t nseg, size_t elem_size,
+                            int key_kind, void *stream) {
+    if (!c || (nseg && !d_seg_offsets)) return TSQS_EINVAL;
+    return ctx_launch(c, base, nmemb_total, d_seg_offsets, nseg, elem_size, key_kind,
+                      (cudaStream_t)stream);
+}
+
+int tsqs_ctx_reserve(tsqs_ctx *c, size_t nmemb_total, size_t nseg, size_t elem_size) {
+    if (!c) return TSQS_EINVAL;
+    int kind = elem_size == 4 ? TSQS_U32 : elem_size == 8 ? TSQS_U64 : elem_size == 16 ? TSQS_U64_U64_REC : 0;
+    const KindOps *o = get_ops(kind);
+    if (!o) return TSQS_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int rc = ctx_init_device(c);
+    if (rc) return rc;
+    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, o->tile);
+}
+
+size_t tsqs_ctx_scratch_bytes(const tsqs_ctx *c) { return c ? c->scratch_bytes : 0; }
+
+size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
+                              const tsqs_plan *plan) {
+    int kind = elem_size == 4 ? TSQS_U32 : elem_size == 8 ? TSQS_U64 : elem_size == 16 ? TSQS_U64_U64_REC : 0;
+    const KindOps *o = get_ops(kind);
+    if (!o) return 0;
+    tsqs_plan p;
+    if (plan) p = *plan; else fill_default_plan(kind, nmemb_total, &p);
+    normalise_plan(&p);
+    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, o->tile).total;
+}
+
+int tsqs_ctx_device_status(tsqs_ctx *c, void *stream) {
+    if (!c) return TSQS_EINVAL;
+    return read_status(c, (cudaStream_t)stream, true);
+}
+
+int tsqs_ctx_stats(tsqs_ctx *c, void *stream, tsqs_stats *out) {
+    if (!c || !out) return TSQS_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    memset(out, 0, sizeof(*out));
+    if (c->device < 0) return TSQS_OK;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (c->ev_valid) CK(cudaEventSynchronize(c->done_ev));
+    Ctl h;
+    CK(cudaMemcpy(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    out->levels = h.levels_done;
+    out->max_frontier = h.max_front;
+    out->partition_keys = h.partition_keys;
+    out->leaf_sorted_keys = h.leaf_sorted;
+    out->leaf_filled_keys = h.leaf_filled;
+    out->leaf_items = h.leaf_items;
+    const uint32_t nl = std::min<uint32_t>(h.level, (uint32_t)kStatLevels);
+    out->level_keys_count = nl;
+    for (uint32_t i = 0; i < nl; i++) out->level_keys[i] = h.level_keys[i];
+    return TSQS_OK;
+}
+
+int tsqs_plan_default(int key_kind, size_t n_hint, tsqs_plan *out) {
+    if (!out || !get_ops(key_kind)) return TSQS_EINVAL;
+    fill_default_plan(key_kind, n_hint, out);
+    normalise_plan(out);
+    return TSQS_OK;
+}
+
+int tsqs_sort(void *base, size_t nmemb, size_t elem_size, int key_kind, void *stream) {
+    tsqs_ctx *c = default_ctx();
+    if (!c) return TSQS_ENOMEM;
+    return tsqs_ctx_sort(c, base, nmemb, elem_size, key_kind, stream);
+}
+
+int tsqs_sort_segmented(void *base, size_t nmemb_total, const uint64_t *d_seg_offsets,
+                        size_t nseg, size_t elem_size, int key_kind, void *stream) {
+    tsqs_ctx *c = default_ctx();
+    if (!c) return TSQS_ENOMEM;
+    return tsqs_ctx_sort_segmented(c, base, nmemb_total, d_seg_offsets, nseg, elem_size,
+                                   key_kind, stream);
+}
+
+void tsqs_free_storage(void) {
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (g_default) {
+        tsqs_ctx_destroy(g_default);
+        g_default = nullptr;
+    }
+}
+
+int tsqs_last_device_status(void *stream) {
+    tsqs_ctx *c = default_ctx();
+    if (!c) return TSQS_ENOMEM;
+    return read_status(c, (cudaStream_t)stream, true);
+}
+
+void tsqs_debug_set_spin_limit(uint32_t polls) { g_debug_spin = polls; }
+void tsqs_debug_withhold_publish(int on) { g_debug_withhold = on ? 1 : 0; }
+
+// ---------------------------------------------------------------------------------
+// host-memory sort: device staging buffer owned by the default context's side store
+// ---------------------------------------------------------------------------------
+
+static std::mutex g_host_mu;
+static void *g_host_dev = nullptr;
+static size_t g_host_dev_bytes = 0;
+
+int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, void *stream) {
+    int rc = validate(h_base, nmemb, elem_size, key_kind);
+    if (rc) return rc;
+    if (nmemb <= 1) return TSQS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    const size_t bytes = nmemb * elem_size;
+    if (bytes > g_host_dev_bytes) {
+        if (g_host_dev) { CK(cudaStreamSynchronize(s)); cudaFree(g_host_dev); g_host_dev = nullptr; g_host_dev_bytes = 0; }
+        if (cudaMalloc(&g_host_dev, bytes) != cudaSuccess) { cudaGetLastError(); return TSQS_ENOMEM; }
+        g_host_dev_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(g_host_dev, h_base, bytes, cudaMemcpyHostToDevice, s));
+    rc = tsqs_sort(g_host_dev, nmemb, elem_size, key_kind, stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h_base, g_host_dev, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TSQS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Instrumented host-driven run (same kernels as the graph, one launch each).
+// ---------------------------------------------------------------------------------
+
+int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
+                        int key_kind, void *stream, float *h_ms, uint64_t *h_keys,
+                        int max_levels, int *levels, float *h_leaf_ms) {
+    if (!c) return TSQS_EINVAL;
+    int rc = validate(base, nmemb, elem_size, key_kind);
+    if (rc) return rc;
+    if (levels) *levels = 0;
+    if (nmemb <= 1) return TSQS_OK;
+    if (nmemb >= (1ull << 31)) return TSQS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const KindOps *o = get_ops(key_kind);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if ((rc = ctx_init_device(c))) return rc;
+    if ((rc = ctx_kind_setup(c, o))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, o->tile))) return rc;
+    Job j;
+    if ((rc = make_job(c, o, base, nmemb, nullptr, 0, &j))) return rc;
+    if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
+    const int k = key_kind;
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    cudaGraphConditionalHandle h = 0;
+    int use_h = 0;
+    unsigned int unused = 0;
+    void *argsf[] = {&pj, &pc, &h, &use_h, &unused};
+    cudaEvent_t ev[4];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
+    CK(cudaLaunchKernel(o->k_init, dim3(c->sms * 2), dim3(256), args2, 0, s));
+    int L = 0;
+    for (;;) {
+        CK(cudaEventRecord(ev[2], s));
+        CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), args2,
+                            (size_t)o->leaf_smem, s));
+        CK(cudaEventRecord(ev[3], s));
+        CK(cudaLaunchKernel(o->k_pivot, dim3(c->sms * 4), dim3(o->pivot_block), args2, 0, s));
+        CK(cudaEventRecord(ev[0], s));
+        CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[k]), dim3(o->part_block), args2, 0, s));
+        CK(cudaEventRecord(ev[1], s));
+        CK(cudaLaunchKernel(o->k_finish, dim3(1), dim3(32), argsf, 0, s));
+        CK(cudaMemcpyAsync(c->h_cont, &c->d_ctl->cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (L < max_levels) {
+            float ms = 0.f, lms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            CK(cudaEventElapsedTime(&lms, ev[2], ev[3]));
+            if (h_ms) h_ms[L] = ms;
+            if (h_leaf_ms) h_leaf_ms[L] = lms;
+        }
+        L++;
+        if (!*c->h_cont) break;
+        if (L > 100000) break;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (h_keys) {
+        Ctl hc;
+        CK(cudaMemcpy(&hc, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < std::min(L, max_levels); i++)
+            h_keys[i] = i < kStatLevels ? hc.level_keys[i] : 0;
+    }
+    if (levels) *levels = L;
+    CK(cudaEventRecord(c->done_ev, s));
+    c->ev_valid = true;
+    return TSQS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Step-level entry points
+// ---------------------------------------------------------------------------------
+
+int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_kind,
+                     uint64_t seg_begin, uint64_t seg_end, int sample_count, uint64_t seed,
+                     uint64_t *h_positions, void *h_pivot, void *stream) {
+    int rc = validate((void *)base, nmemb, elem_size, key_kind);
+    if (rc) return rc;
+    if (seg_end <= seg_begin || seg_end > nmemb || !h_positions || !h_pivot) return TSQS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    tsqs_ctx *c = default_ctx();
+    const KindOps *o = get_ops(key_kind);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if ((rc = ctx_init_device(c))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, o->tile))) return rc;
+    Job j;
+    if ((rc = make_job(c, o, (void *)base, nmemb, nullptr, 0, &j))) return rc;
+    const Layout L = make_layout(nmemb, 1, elem_size, c->plan, o->tile);
+    char *misc = c->scratch + L.misc_off;
+    uint64_t *d_offs = (uint64_t *)misc;
+    uint64_t *d_pos = (uint64_t *)(misc + 64);
+    void *d_piv = misc + 64 + 8 * kMaxSamples + 64;
+    const uint64_t offs[2] = {seg_begin, seg_end};
+    if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
+    CK(cudaMemcpyAsync(d_offs, offs, sizeof(offs), cudaMemcpyHostToDevice, s));
+    j.seg_offsets = d_offs;
+    j.nseg = 1;
+    j.samples = (uint32_t)(sample_count > 0 ? sample_count : c->plan.sample_count);
+    j.seed = seed;
+    j.dbg_positions = d_pos;
+    j.dbg_pivot_out = d_piv;
+    CK(cudaMemsetAsync(d_pos, 0xFF, 8 * kMaxSamples, s));
+    k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    CK(cudaLaunchKernel(o->k_dbg_pivot, dim3(1), dim3(32), args2, 0, s));
+    uint64_t pos[kMaxSamples];
+    CK(cudaMemcpyAsync(pos, d_pos, sizeof(pos), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h_pivot, d_piv, elem_size, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    uint32_t S = j.samples > (uint32_t)kMaxSamples ? (uint32_t)kMaxSamples : j.samples;
+    for (uint32_t i = 0; i < (uint32_t)kMaxSamples; i++) h_positions[i] = i < S ? pos[i] : ~0ull;
+    CK(cudaEventRecord(c->done_ev, s));
+    c->ev_valid = true;
+    return TSQS_OK;
+}
+
+int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_size,
+                         int key_kind, const uint64_t *d_seg_offsets, size_t nseg,
+                         const void *d_pivots, uint64_t *d_counts, void *stream) {
+    int rc = validate((void *)src, nmemb, elem_size, key_kind);
+    if (rc) return rc;
+    if (!dst || !d_seg_offsets || !d_pivots || !d_counts || nseg == 0) return TSQS_EINVAL;
+    if (((uintptr_t)src & 15u) != ((uintptr_t)dst & 15u)) return TSQS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    tsqs_ctx *c = default_ctx();
+    const KindOps *o = get_ops(key_kind);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if ((rc = ctx_init_device(c))) return rc;
+    if ((rc = ctx_kind_setup(c, o))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, o->tile))) return rc;
+    Job j;
+    if ((rc = make_job(c, o, (void *)src, nmemb, d_seg_offsets, nseg, &j))) return rc;
+    j.alt = dst;
+    j.dbg_pivots = d_pivots;
+    j.dbg_counts = d_counts;
+    j.pad |= 1u;                                  // no epilogue: one level only
+    if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
+    k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    const unsigned gs = (unsigned)std::min<size_t>(nseg, (size_t)c->sms * 8);
+    CK(cudaLaunchKernel(o->k_dbg_setup_partition, dim3(gs), dim3(256), args2, 0, s));
+    CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[key_kind]), dim3(o->part_block), args2, 0, s));
+    CK(cudaLaunchKernel(o->k_dbg_counts, dim3(c->sms), dim3(256), args2, 0, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(c->done_ev, s));
+    c->ev_valid = true;
+    return TSQS_OK;
+}
+
+int tsqs_debug_small_sort(void *base, size_t nmemb, size_t elem_size, int key_kind,
+                          const uint64_t *d_seg_offsets, size_t nseg, void *stream) {
+    tsqs_ctx *c = default_ctx();
+    int rc = tsqs_ctx_sort_segmented(c, base, nmemb, d_seg_offsets, nseg, elem_size, key_kind, stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return TSQS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// tsqs_internal.h -- structures shared by the host runtime and the kernels.
+//
+// One sort is a level-synchronous walk over a device-built work queue:
+//   frontier[par]  segments larger than the small threshold waiting for a partition
+//                  level (the recursion of Fig. 1 turned into a breadth-first queue);
+//   leaves[par]    work for the on-chip pass: segments of <= small threshold elements
+//                  to sort (Section IV's role) and runs of =p to fill with p
+//                  (Section III.F: the equals are placed once and never compared again).
+// Level L reads buffer L%2 (0 = caller's array, 1 = scratch) and writes buffer
+// (L+1)%2; every element reaches its final place in the caller's array exactly once,
+// through a leaf sort or an =p fill.
+#pragma once
+#include <stdint.h>
+
+namespace tsqs {
+
+constexpr int kMaxSamples = 63;
+constexpr uint32_t kFillChunk = 16384;      // =p fills are split into items of this size
+constexpr int kMaxSmall = 4096;             // largest on-chip segment
+constexpr int kStatLevels = 64;
+
+enum LeafKind : uint32_t { LEAF_SORT = 0, LEAF_FILL = 1 };
+
+// A segment [begin, end) waiting for a partition level.
+struct SegDesc {
+    uint64_t begin, end;
+    int64_t  s0;              // element index where tile 0 starts (16-byte aligned, <= begin)
+    uint32_t tile_begin;      // first global tile id of this segment in its level
+    uint32_t ntiles;
+    uint64_t piv_lo, piv_hi;  // canonical pivot (hi used by 16-byte records only)
+};
+
+struct LeafItem {
+    uint64_t begin;
+    uint32_t len;
+    uint32_t kind;            // LeafKind
+    uint64_t v_lo, v_hi;      // canonical fill value for LEAF_FILL
+};
+
+// Mutable device state of one sort; zeroed by the setup kernel of every call.
+struct Ctl {
+    uint32_t level;           // current level (iteration of the level loop)
+    uint32_t status;          // sticky tsqs_status of the device side
+    uint32_t tile_claim;      // partition tiles claimed in this level
+    uint32_t leaf_claim;      // leaf items claimed in this level
+    uint32_t seg_claim;       // frontier segments claimed by the pivot kernel
+    uint32_t cont;            // level loop continues (host-driven mode reads it)
+    uint32_t nfront[2];
+    uint32_t ntiles[2];
+    uint32_t nleaf[2];
+    uint32_t max_front;
+    uint32_t levels_done;
+    uint64_t front_keys[2];
+    uint64_t partition_keys;
+    uint64_t leaf_sorted, leaf_filled, leaf_items;
+    uint64_t level_keys[kStatLevels];
+};
+
+// Per-call description, written by the setup kernel and read by every kernel.
+struct Job {
+    void *base;               // buffer 0: the caller's array
+    void *alt;                // buffer 1: scratch with the same 16-byte phase as base
+    uint64_t n;               // elements addressable in base (and alt)
+    const uint64_t *seg_offsets;   // nullptr: one segment [0, n)
+    uint64_t nseg;
+    SegDesc *front[2];
+    LeafItem *leaves[2];
+    uint32_t *tile_seg;       // tile id -> frontier index, current level
+    unsigned long long *tile_status;   // decoupled look-back words, current level
+    uint32_t *seg_done;       // finished tiles per frontier segment
+    uint32_t cap_front, cap_tiles, cap_leaves;
+    uint32_t small_T;         // on-chip threshold
+    uint32_t samples;         // pivot sample count (odd, <= kMaxSamples)
+    uint32_t vec_off;         // (address of base / elem_size) mod (16 / elem_size)
+    uint32_t spin_limit;      // polls before a look-back wait gives up
+    uint32_t pad;             // bit 0: skip the segment epilogue (step-level test of one
+                              // level); bit 1: tile id 1 withholds its look-back status
+                              // (test of the bounded wait)
+    uint32_t max_levels;      // level cap; exceeding it stops the loop with an error
+    uint32_t pad2;
+    uint64_t seed;            // sample jitter seed
+    // step-level test hooks
+    const void *dbg_pivots;   // debug partition: pivots of the given segments
+    uint64_t *dbg_counts;     // debug partition: (#<p, #>p) per segment
+    uint64_t *dbg_positions;  // debug pivot: sample positions
+    void *dbg_pivot_out;      // debug pivot: chosen pivot (original representation)
+};
+
+// Kernel entry points of one key kind (filled by the per-kind translation units).
+struct KindOps {
+    int kind;
+    int elem_size;
+    int tile;                 // keys per partition tile
+    int part_block, leaf_block, pivot_block;
+    int leaf_smem;            // dynamic shared memory of the leaf kernel
+    const void *k_init, *k_leaf, *k_pivot, *k_partition, *k_finish;
+    const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
+};
+
+const KindOps *ops_k4(int kind);
+const KindOps *ops_k8(int kind);
+const KindOps *ops_k16(int kind);
+
+}  // namespace tsqs
