@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the three-way partition sort on GB300.
+
+Default workload (the headline): 2^27 int32 keys uniform over [-2^31, 2^31), seed 1,
+sorted ascending by tsqs_sort.  Each timed step sorts its own freshly copied input
+(512 MiB, larger than L2), staged in HBM before the timed region, so no step sees a
+sorted array or a warm L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload {uniform,patterns,c1,records,floats,batched,serving}]
+Under torchrun each rank sorts its own array (replicas; the path does not shard), and
+rank 0 prints one JSON line with the whole-job throughput (keys of all ranks / the
+slowest rank's time).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mkeys/s & % HBM roofline, 2^27 int32; batched vs per-call segs/s; p99 latency"
+UNIT = "Mkeys/s"
+N_HEADLINE = 1 << 27
+SMALL_T = 4096
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one partition launch per key it read,
+# from an ncu capture of the kernel source with this sha256 prefix (null when the
+# kernel changed since).
+NCU_TRAFFIC = {"kernels_sha": None, "bytes_per_key": None, "source": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tsqs", choices=["tsqs", "reference"])
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "patterns", "c1", "records", "floats", "batched", "serving"])
+    ap.add_argument("--n", type=int, default=N_HEADLINE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def p_min(n: int, T: int = SMALL_T) -> int:
+    """Unavoidable passes of a perfect-median three-way quicksort that finishes parts
+    of <= T on chip: ceil(log2(n / T)) partition levels plus one on-chip pass."""
+    return max(0, math.ceil(math.log2(n / T))) + 1 if n > T else 1
+
+
+def kernels_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("tsqs_kernels.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_1505_00558_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------
+# distributed plumbing
+# ------------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, gpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------
+# CPU legs (oracle; the only places bench.py runs oracle/)
+# ------------------------------------------------------------------------------
+
+def oracle_rate(keys: np.ndarray, budget_s: float = 12.0, chunk: int = 1 << 24):
+    """Times the oracle single-threaded on consecutive chunks of keys (each chunk is
+    sorted on its own) until budget_s of CPU time; returns (Mkeys/s, sample text)."""
+    import oracle
+    oracle.build()
+    done, t_tot, chunks = 0, 0.0, 0
+    off = 0
+    while t_tot < budget_s and off < len(keys):
+        part = np.ascontiguousarray(keys[off:off + chunk].copy())
+        t0 = time.perf_counter()
+        oracle.tsqs_sort(part, oracle.KIND_I32)
+        t_tot += time.perf_counter() - t0
+        done += len(part)
+        off += chunk
+        chunks += 1
+    sample = (f"{chunks} independent sorts of {chunk} keys (the first {done} keys of the "
+              f"workload), oracle single-threaded")
+    return done / t_tot / 1e6, sample, t_tot
+
+
+def reference_arm(args, dist):
+    if dist.rank != 0:
+        return
+    from workloads import int32_pattern
+    n = args.n
+    keys = int32_pattern("random", min(n, 1 << 22) * 8, seed=1)
+    chunk = 1 << 22
+    import oracle
+    oracle.build()
+    for w in range(args.warmup):
+        part = np.ascontiguousarray(keys[:chunk].copy())
+        oracle.tsqs_sort(part, oracle.KIND_I32)
+    times = []
+    for s in range(args.steps):
+        off = (s % 8) * chunk
+        part = np.ascontiguousarray(keys[off:off + chunk].copy())
+        t0 = time.perf_counter()
+        oracle.tsqs_sort(part, oracle.KIND_I32)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * chunk / tot / 1e6
+    sample = f"each step: the oracle sorts {chunk} keys of the workload single-threaded"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "2^27 int32 uniform random seed 1 (bounded sample per step)",
+                       "n_per_step": chunk},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------
+
+def stage_copies(torch, src, count):
+    return [src.clone() for _ in range(count)]
+
+
+def time_sorts(torch, T, copies, kind, warmup, dist, records=False):
+    """Sorts warmup copies untimed, then every remaining copy inside one timed region
+    bracketed by a barrier and synchronize; returns (total ms, per-step ms list)."""
+    stream = torch.cuda.current_stream()
+    for i in range(warmup):
+        T.sort_(copies[i], kind=kind)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(copies) - warmup + 1)]
+    evs[0].record(stream)
+    for j, c in enumerate(copies[warmup:]):
+        T.sort_(c, kind=kind)
+        evs[j + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    total = evs[0].elapsed_time(evs[-1])
+    per = [evs[j].elapsed_time(evs[j + 1]) for j in range(len(evs) - 1)]
+    return total, per
+
+
+def gpu_arm(args, dist):
+    import torch
+    torch.cuda.set_device(dist.local)
+    import paper_1505_00558_gb300 as T
+    from workloads import int32_pattern
+    T.lib()
+    hbm, hbm_src = peaks()
+    n = args.n
+    K, W = args.steps, args.warmup
+    x = int32_pattern("random", n, seed=1 + dist.rank * 0)
+    src = torch.from_numpy(x).cuda()
+    copies = stage_copies(torch, src, K + W)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    total_ms, per = time_sorts(torch, T, copies, T.TSQS_I32, W, dist)
+    clk = clocks.stop()
+    status = T.last_device_status()
+    ok = bool((copies[-1][1:] >= copies[-1][:-1]).all().item()) and status == 0
+    total_ms = dist.max(total_ms)
+    keys_all = dist.sum(float(K * n))
+    value = keys_all / (total_ms * 1e-3) / 1e6
+    ms_step = total_ms / K
+
+    # launches per sort: setup + init + 4 per level iteration (leaf, pivot, partition, finish)
+    ctx = T.Context()
+    chk = src.clone()
+    T.sort_(chk, kind=T.TSQS_I32, ctx=ctx)
+    st = ctx.stats()
+    iters = len(st["level_keys"]) if st["level_keys"] else st["levels"] + 1
+    launches_per_sort = 2 + 4 * iters
+    del copies
+
+    # dominant kernel: partition levels, timed one launch at a time with CUDA events
+    part_ms, part_keys = [], []
+    leaf_ms = []
+    for r in range(3):
+        c = src.clone()
+        ms, keys, lms = ctx.sort_timed(c, kind=T.TSQS_I32)
+        if r == 0:
+            continue                                     # first instrumented run warms up
+        part_ms += ms
+        part_keys += keys
+        leaf_ms += lms
+    busy = [(m, k) for m, k in zip(part_ms, part_keys) if k > 0]
+    alg_bytes = sum(2 * 4 * k for _, k in busy)
+    t_part = sum(m for m, _ in busy) * 1e-3
+    achieved = alg_bytes / t_part / 1e9 if t_part > 0 else None
+    n_launch = len(busy)
+    sha = kernels_sha()
+    traffic = None
+    if NCU_TRAFFIC["kernels_sha"] == sha and NCU_TRAFFIC["bytes_per_key"]:
+        traffic = NCU_TRAFFIC["bytes_per_key"] * (sum(k for _, k in busy) / max(1, n_launch))
+    roofline = {"bound": "hbm", "kernel": "k_partition (one launch per level)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None,
+                "traffic": traffic, "peak_source": hbm_src,
+                "alg_bytes_per_launch": alg_bytes / max(1, n_launch),
+                "avg_launch_ms": t_part * 1e3 / max(1, n_launch),
+                "note": "8 bytes (one 4-byte read + one 4-byte write) per key partitioned in the "
+                        "launch; launch times from CUDA events around each partition launch"}
+    pm = p_min(n)
+    whole_alg = pm * 2 * n * 4
+    whole = {"p_min": pm, "alg_bytes": whole_alg,
+             "achieved_gbs": whole_alg / (ms_step * 1e-3) / 1e9,
+             "frac_of_measured": whole_alg / (ms_step * 1e-3) / 1e9 / hbm,
+             "frac_of_nominal_8tbs": whole_alg / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+             "roofline_mkeys": hbm * 1e9 / (2 * pm * 4) / 1e6,
+             "partition_ms_per_sort": sum(m for m, _ in busy) / 2,
+             "leaf_ms_per_sort": sum(leaf_ms) / 2}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        hsrc = torch.from_numpy(x).pin_memory()
+        hbuf = torch.empty_like(hsrc).pin_memory()
+        s = torch.cuda.current_stream()
+        lib = T.lib()
+        times = []
+        for i in range(W + max(3, K // 6)):
+            hbuf.copy_(hsrc)
+            t0 = time.perf_counter()
+            rc = lib.tsqs_sort_host(ctypes.c_void_p(hbuf.data_ptr()), n, 4, T.TSQS_I32,
+                                    ctypes.c_void_p(s.cuda_stream))
+            t1 = time.perf_counter()
+            assert rc == 0
+            if i >= W:
+                times.append(t1 - t0)
+        e2e_ok = bool((hbuf[1:] >= hbuf[:-1]).all().item())
+        tt = dist.max(sum(times))
+        e2e = {"value": dist.sum(float(len(times) * n)) / tt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4,
+               "api": "tsqs_sort_host (pinned host array in, sorted host array out)",
+               "sorted": e2e_ok}
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        rate, sample, t_cpu = oracle_rate(x, budget_s=10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": t_cpu}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": K, "warmup": W, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "2^27 int32 uniform random [-2^31, 2^31), seed 1, tsqs_sort",
+                       "n": n, "parallelism": f"replicas x{dist.world}",
+                       "l2": "inputs larger than L2: every step sorts its own fresh 512 MiB copy",
+                       "small_threshold": SMALL_T},
+            "roofline": roofline, "roofline_whole_sort": whole, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_sort * K,
+            "sorted": ok, "device_status": status,
+            "per_step_ms": {"median": statistics.median(per), "min": min(per), "max": max(per)},
+            "levels": st["levels"], "kernels_sha": sha}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def other_workload(args, dist):
+    raise SystemExit(f"workload {args.workload} is not wired into bench.py yet")
+
+
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            reference_arm(args, dist)
+        elif args.workload == "uniform":
+            gpu_arm(args, dist)
+        else:
+            other_workload(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,12 @@ typedef struct {
     int32_t  small_threshold;  /* segments of <= this many elements finish on chip (<= 4096) */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
     int32_t  sample_count;     /* pivot sample size: 15, 31 or 63                      */
+    int32_t  offset_mode;      /* where a tile writes its <p and >p runs:
+                                  0 = reserved with one 64-bit atomic on a per-segment
+                                      cursor (default; tiles never wait on each other),
+                                  1 = decoupled look-back over (#<p, #>p) in tile order
+                                      (deterministic intermediate layout)              */
+    int32_t  pad;
     uint64_t seed;             /* seed of the jittered sample positions (Section V.C)   */
 } tsqs_plan;
 

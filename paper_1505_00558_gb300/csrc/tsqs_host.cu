@@ -45,7 +45,7 @@ size_t kind_size(int kind) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t alt_off, front_off[2], leaves_off[2], tseg_off, tstat_off, done_off, misc_off, total;
+    size_t alt_off, front_off[2], leaves_off[2], tseg_off, tstat_off, done_off, cursor_off, misc_off, total;
     uint32_t cap_front, cap_tiles, cap_leaves;
 };
 
@@ -73,6 +73,7 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     L.tseg_off = off;           off = align_up(off + ct * sizeof(uint32_t), 256);
     L.tstat_off = off;          off = align_up(off + ct * sizeof(unsigned long long), 256);
     L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
+    L.cursor_off = off;         off = align_up(off + cf * sizeof(unsigned long long), 256);
     L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
     L.total = off;
     return L;
@@ -84,6 +85,8 @@ void fill_default_plan(int key_kind, size_t, tsqs_plan *p) {
     p->small_threshold = kMaxSmall;
     p->ctas_per_sm = 0;           // occupancy-derived
     p->sample_count = 31;
+    p->offset_mode = 0;
+    p->pad = 0;
     p->seed = 0x5EED5EED12345678ull;
 }
 
@@ -98,6 +101,7 @@ void normalise_plan(tsqs_plan *p) {
     if ((p->sample_count & 1) == 0) p->sample_count -= 1;
     if (p->seed == 0) p->seed = d.seed;
     if (p->ctas_per_sm < 0) p->ctas_per_sm = 0;
+    if (p->offset_mode != 1) p->offset_mode = 0;
 }
 
 uint32_t g_debug_spin = 0;        // 0 = default
@@ -153,8 +157,9 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     const int k = o->kind;
     if (c->attrs_set[k]) return TSQS_OK;
     CK(cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem));
+    CK(cudaFuncSetAttribute(o->k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, o->part_smem));
     int occ_p = 0, occ_l = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, o->k_partition, o->part_block, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, o->k_partition, o->part_threads, o->part_smem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem));
     if (c->plan.ctas_per_sm > 0) occ_p = std::min(occ_p, c->plan.ctas_per_sm);
     c->part_grid[k] = std::max(1, occ_p) * c->sms;
@@ -211,6 +216,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->tile_seg = (uint32_t *)(c->scratch + L.tseg_off);
     j->tile_status = (unsigned long long *)(c->scratch + L.tstat_off);
     j->seg_done = (uint32_t *)(c->scratch + L.done_off);
+    j->seg_cursor = (unsigned long long *)(c->scratch + L.cursor_off);
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
@@ -223,6 +229,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     unsigned lg = 1;
     while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
     j->max_levels = 256u + 8u * lg;
+    j->offset_mode = (c->plan.offset_mode == 1 || g_debug_withhold) ? 1u : 0u;
     j->seed = c->plan.seed;
     return TSQS_OK;
 }
@@ -272,7 +279,8 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_partition;
     kp.gridDim = dim3(c->part_grid[k]);
-    kp.blockDim = dim3(o->part_block);
+    kp.blockDim = dim3(o->part_threads);
+    kp.sharedMemBytes = (unsigned)o->part_smem;
     kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_part, body, &n_piv, 1, &kp));
     int use_h = 1;
@@ -280,8 +288,8 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     void *argsf[] = {&pj, &pc, &h, &use_h, &unused};
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_finish;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(32);
+    kp.gridDim = dim3(c->sms);
+    kp.blockDim = dim3(128);
     kp.kernelParams = argsf;
     CK(cudaGraphAddKernelNode(&n_fin, body, &n_part, 1, &kp));
 
@@ -577,9 +585,10 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
         CK(cudaEventRecord(ev[3], s));
         CK(cudaLaunchKernel(o->k_pivot, dim3(c->sms * 4), dim3(o->pivot_block), args2, 0, s));
         CK(cudaEventRecord(ev[0], s));
-        CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[k]), dim3(o->part_block), args2, 0, s));
+        CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[k]), dim3(o->part_threads), args2,
+                            (size_t)o->part_smem, s));
         CK(cudaEventRecord(ev[1], s));
-        CK(cudaLaunchKernel(o->k_finish, dim3(1), dim3(32), argsf, 0, s));
+        CK(cudaLaunchKernel(o->k_finish, dim3(c->sms), dim3(128), argsf, 0, s));
         CK(cudaMemcpyAsync(c->h_cont, &c->d_ctl->cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (L < max_levels) {
@@ -674,7 +683,6 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     j.alt = dst;
     j.dbg_pivots = d_pivots;
     j.dbg_counts = d_counts;
-    j.pad |= 1u;                                  // no epilogue: one level only
     if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
     k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
     Job *pj = c->d_job;
@@ -682,7 +690,8 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     void *args2[] = {&pj, &pc};
     const unsigned gs = (unsigned)std::min<size_t>(nseg, (size_t)c->sms * 8);
     CK(cudaLaunchKernel(o->k_dbg_setup_partition, dim3(gs), dim3(256), args2, 0, s));
-    CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[key_kind]), dim3(o->part_block), args2, 0, s));
+    CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[key_kind]), dim3(o->part_threads), args2,
+                        (size_t)o->part_smem, s));
     CK(cudaLaunchKernel(o->k_dbg_counts, dim3(c->sms), dim3(256), args2, 0, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaEventRecord(c->done_ev, s));

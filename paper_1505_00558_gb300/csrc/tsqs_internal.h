@@ -50,6 +50,8 @@ struct Ctl {
     uint32_t nleaf[2];
     uint32_t max_front;
     uint32_t levels_done;
+    uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
+    uint32_t pad_;
     uint64_t front_keys[2];
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;
@@ -68,16 +70,16 @@ struct Job {
     uint32_t *tile_seg;       // tile id -> frontier index, current level
     unsigned long long *tile_status;   // decoupled look-back words, current level
     uint32_t *seg_done;       // finished tiles per frontier segment
+    unsigned long long *seg_cursor;    // reserved (#<p | #>p << 32) per frontier segment
     uint32_t cap_front, cap_tiles, cap_leaves;
     uint32_t small_T;         // on-chip threshold
     uint32_t samples;         // pivot sample count (odd, <= kMaxSamples)
     uint32_t vec_off;         // (address of base / elem_size) mod (16 / elem_size)
     uint32_t spin_limit;      // polls before a look-back wait gives up
-    uint32_t pad;             // bit 0: skip the segment epilogue (step-level test of one
-                              // level); bit 1: tile id 1 withholds its look-back status
-                              // (test of the bounded wait)
+    uint32_t pad;             // bit 1: tile id 1 withholds its look-back status (test of
+                              // the bounded wait)
     uint32_t max_levels;      // level cap; exceeding it stops the loop with an error
-    uint32_t pad2;
+    uint32_t offset_mode;     // 0: per-segment atomic cursor, 1: decoupled look-back
     uint64_t seed;            // sample jitter seed
     // step-level test hooks
     const void *dbg_pivots;   // debug partition: pivots of the given segments
@@ -92,6 +94,8 @@ struct KindOps {
     int elem_size;
     int tile;                 // keys per partition tile
     int part_block, leaf_block, pivot_block;
+    int part_threads;         // consumer warps + one producer warp
+    int part_smem;            // dynamic shared memory of the partition kernel
     int leaf_smem;            // dynamic shared memory of the leaf kernel
     const void *k_init, *k_leaf, *k_pivot, *k_partition, *k_finish;
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;

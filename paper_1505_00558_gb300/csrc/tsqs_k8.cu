@@ -5,7 +5,7 @@ namespace tsqs {
 
 namespace {
 constexpr int kPartBlock = 256, kItems = 8, kTile = kPartBlock * kItems;
-constexpr int kLeafBlock = 512, kPivotBlock = 256;
+constexpr int kLeafBlock = 256, kPivotBlock = 256, kNBuf = 3;
 
 template <int KIND>
 KindOps make_ops() {
@@ -14,14 +14,16 @@ KindOps make_ops() {
     o.elem_size = 8;
     o.tile = kTile;
     o.part_block = kPartBlock;
+    o.part_threads = kPartBlock + 32;
+    o.part_smem = (int)PartLayout<KIND, kPartBlock, kItems, kNBuf>::bytes;
     o.leaf_block = kLeafBlock;
     o.pivot_block = kPivotBlock;
-    o.leaf_smem = kMaxSmall * (int)sizeof(typename Key<KIND>::C);
+    o.leaf_smem = (kMaxSmall + kMaxSmall / 32) * (int)sizeof(typename Key<KIND>::C);
     o.k_init = (const void *)k_init<KIND, kTile>;
-    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock>;
+    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, 2>;
     o.k_pivot = (const void *)k_pivot<KIND, kTile>;
-    o.k_partition = (const void *)k_partition<KIND, kPartBlock, kItems>;
-    o.k_finish = (const void *)k_finish;
+    o.k_partition = (const void *)k_partition<KIND, kPartBlock, kItems, kNBuf>;
+    o.k_finish = (const void *)k_level_end<KIND, kTile>;
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND, kTile>;
     o.k_dbg_counts = (const void *)k_dbg_counts;
     o.k_dbg_pivot = (const void *)k_dbg_pivot<KIND>;

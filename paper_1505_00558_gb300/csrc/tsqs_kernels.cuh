@@ -13,7 +13,8 @@
 //                again; offsets come from a decoupled look-back over (#<p, #>p), and
 //                the last tile of a segment pushes its children (the recursion on
 //                [a, l] and [r, b] of Section III.F) to the next level's queues
-//   k_finish     advances the level and decides whether the loop continues
+//   k_level_end  pushes every segment's children and =p fill, then advances the
+//                level and decides whether the loop continues
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -135,6 +136,16 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
 __device__ __forceinline__ void set_status(Ctl *ctl, uint32_t code) {
     atomicCAS(&ctl->status, 0u, code);
 }
+// Block-uniform read of the sticky status: every thread of the block gets the same
+// answer, so an early return never splits a warp or a barrier.
+__device__ __forceinline__ bool block_aborted(const Ctl *ctl) {
+    __shared__ uint32_t s_abort;
+    if (threadIdx.x == 0) s_abort = *(volatile const uint32_t *)&ctl->status;
+    __syncthreads();
+    const bool a = s_abort != 0u;
+    __syncthreads();
+    return a;
+}
 // SplitMix64 finaliser, used to jitter sample positions.
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -161,6 +172,23 @@ __device__ __forceinline__ uint32_t tiles_for(uint64_t end, int64_t s0, int tile
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
 __device__ __forceinline__ unsigned long long lb_pack(unsigned long long flag, uint64_t lt, uint64_t gt) {
     return flag | ((lt & 0x7FFFFFFFull) << 31) | (gt & 0x7FFFFFFFull);
+}
+
+// Final (#<p, #>p) of a segment once all its tiles are counted: the cursor in atomic
+// mode, the last tile's inclusive prefix in look-back mode.  False if not available.
+__device__ __forceinline__ bool seg_totals(const Job *job, uint32_t si, uint32_t tile_begin,
+                                           uint32_t ntiles, uint64_t &nlt, uint64_t &ngt) {
+    if (job->offset_mode == 0u) {
+        const unsigned long long c = ld_relaxed(job->seg_cursor + si);
+        nlt = c & 0xFFFFFFFFull;
+        ngt = c >> 32;
+        return true;
+    }
+    if (ntiles == 0) { nlt = ngt = 0; return true; }
+    const unsigned long long w = ld_relaxed(job->tile_status + tile_begin + ntiles - 1);
+    nlt = (w >> 31) & 0x7FFFFFFFull;
+    ngt = w & 0x7FFFFFFFull;
+    return (w >> 62) == 2ull;
 }
 
 // Pushes [b, e) to the next level: frontier if larger than small_T, leaf otherwise.
@@ -278,7 +306,7 @@ template <int KIND, int TILE>
 __global__ void k_pivot(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     const int par = ctl->level & 1;
-    if (*(volatile uint32_t *)&ctl->status) return;        // queues may be inconsistent
+    if (block_aborted(ctl)) return;                         // queues may be inconsistent
     const uint32_t nf = min(ctl->nfront[par], job->cap_front);
     const typename K::S *src = buffer<K>(job, par);
     for (uint32_t si = blockIdx.x; si < nf; si += gridDim.x) {
@@ -289,11 +317,12 @@ __global__ void k_pivot(const Job *__restrict__ job, Ctl *ctl) {
             const typename K::C p = sample_pivot<K>(src, b, e, job->samples, job->seed, nullptr);
             if (threadIdx.x == 0) c_words(p, d->piv_lo, d->piv_hi);
         }
+        const bool lb = job->offset_mode != 0u;
         for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
             job->tile_seg[tb + t] = si;
-            job->tile_status[tb + t] = 0ull;
+            if (lb) job->tile_status[tb + t] = 0ull;
         }
-        if (threadIdx.x == 0) job->seg_done[si] = 0u;
+        if (threadIdx.x == 0) { job->seg_done[si] = 0u; job->seg_cursor[si] = 0ull; }
     }
 }
 
@@ -351,214 +380,405 @@ __device__ __forceinline__ void lookback(const unsigned long long *status, uint3
 }
 
 // ---------------------------------------------------------------------------------
-// Partition (persistent): tiles of TILE = BLOCK * ITEMS keys claimed in order.
+// Async-proxy helpers: 1-D bulk copies (TMA) completing on shared-memory mbarriers.
 // ---------------------------------------------------------------------------------
 
-template <int KIND, int BLOCK, int ITEMS>
-struct PartSmem {
-    using S = typename Key<KIND>::S;
-    S stage[BLOCK * ITEMS];
-    uint32_t wsum[BLOCK / 32];
-    uint32_t tile, tot, last, nch;
-    unsigned long long ex_lt, ex_gt;
-    uint64_t eqb, eqe, fb;
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }"
+                 ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_addr(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` try_wait rounds (each blocks for a short,
+// hardware-defined time); returns false then.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; i++)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Barrier among the consumer warps only (the producer warp never joins it).
+template <int N>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// ---------------------------------------------------------------------------------
+// Partition (persistent, warp-specialised).
+//   producer warp   claims tiles in order, reads each tile's segment, and stages the
+//                   tile's 16-byte-aligned interior into a ring of NBUF shared-memory
+//                   buffers with one bulk copy (TMA), NBUF-1 tiles ahead
+//   consumer warps  classify the tile against p, scan the packed counts, stage the
+//                   <p / >p elements back into the same buffer while warp 0 runs the
+//                   decoupled look-back, then write both runs out coalesced
+// Tiles are claimed in increasing order and every CTA processes its tiles in claim
+// order, so the lowest unpublished tile is always one a consumer is working on: the
+// look-back always makes progress.
+// ---------------------------------------------------------------------------------
+
+struct TileMeta {
+    int64_t t0, cs, ce;            // tile origin, bulk-copied element range [cs, ce)
+    uint64_t sb, se;               // segment bounds
+    uint64_t piv_lo, piv_hi;
+    uint32_t tile, si, tl, ntiles_seg, tile_begin, valid;
 };
 
-template <int KIND, int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) k_partition(const Job *__restrict__ job, Ctl *ctl) {
+template <int KIND, int BLOCK, int ITEMS, int NBUF>
+struct PartLayout {
+    using S = typename Key<KIND>::S;
+    static constexpr int TILE = BLOCK * ITEMS;
+    static constexpr int NW = BLOCK / 32;
+    static constexpr size_t buf_bytes = (size_t)TILE * sizeof(S);
+    static constexpr size_t off_bar = NBUF * buf_bytes;
+    static constexpr size_t off_meta = off_bar + 2 * NBUF * sizeof(unsigned long long);
+    static constexpr size_t off_misc = off_meta + NBUF * sizeof(TileMeta);
+    static constexpr size_t bytes = off_misc + 128 + NW * sizeof(uint32_t);
+};
+
+struct PartMisc {
+    unsigned long long ex_lt, ex_gt;
+    uint32_t total, pad;
+};
+
+template <int KIND, int BLOCK, int ITEMS, int NBUF>
+__global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
-    constexpr int TILE = BLOCK * ITEMS, V = K::V, NV = ITEMS / V, NW = BLOCK / 32;
-    static_assert(ITEMS % V == 0 && ITEMS <= 32 && TILE < 65536, "tile shape");
-    __shared__ __align__(16) PartSmem<KIND, BLOCK, ITEMS> sm;
+    using LY = PartLayout<KIND, BLOCK, ITEMS, NBUF>;
+    constexpr int TILE = LY::TILE, V = K::V, NW = LY::NW;
+    static_assert(ITEMS <= 32 && TILE < 65536 && (TILE % V) == 0, "tile shape");
+    extern __shared__ __align__(128) unsigned char psm[];
+    S *bufs = reinterpret_cast<S *>(psm);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(psm + LY::off_bar);
+    unsigned long long *empty = full + NBUF;
+    TileMeta *meta = reinterpret_cast<TileMeta *>(psm + LY::off_meta);
+    PartMisc *misc = reinterpret_cast<PartMisc *>(psm + LY::off_misc);
+    uint32_t *wsum = reinterpret_cast<uint32_t *>(psm + LY::off_misc + 128);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int par = ctl->level & 1;
-    if (*(volatile uint32_t *)&ctl->status) return;        // queues may be inconsistent
+    if (block_aborted(ctl)) return;                         // queues may be inconsistent
     const uint32_t ntiles = min(ctl->ntiles[par], job->cap_tiles);
     const uint32_t nfront = min(ctl->nfront[par], job->cap_front);
     const S *__restrict__ src = buffer<K>(job, par);
     S *__restrict__ dst = buffer<K>(job, par ^ 1);
-    const bool epilogue = (job->pad & 1u) == 0;      // debug runs skip the epilogue
+    const uint32_t wait_limit = 1u << 20;
 
-    for (;;) {
-        if (tid == 0) sm.tile = atomicAdd(&ctl->tile_claim, 1u);
-        __syncthreads();
-        const uint32_t tile = sm.tile;
-        if (tile >= ntiles) break;
-        const uint32_t si = job->tile_seg[tile];
-        if (si >= nfront) {                              // cannot happen with a sane queue
-            if (tid == 0) set_status(ctl, TSQS_EINTERNAL);
-            __syncthreads();
-            continue;
-        }
-        const SegDesc sd = job->front[par][si];
-        const C piv = c_from<C>(sd.piv_lo, sd.piv_hi);
-        const uint32_t tl = tile - sd.tile_begin;
-        const int64_t t0 = sd.s0 + (int64_t)tl * TILE;
-        const int64_t sb = (int64_t)sd.begin, se = (int64_t)sd.end;
+    if (tid == 0) {
+        for (int s = 0; s < NBUF; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        fence_mbar_init();
+    }
+    __syncthreads();
 
-        // ---- load and classify: 16-byte loads inside the segment, scalar at its ends
-        S v[ITEMS];
-        uint32_t ltm = 0, gtm = 0;
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            const int64_t e0 = t0 + (int64_t)(k * BLOCK + tid) * V;
-            if (e0 >= sb && e0 + V <= se) {
-                load_vec<S, V>(src + e0, &v[k * V]);
-#pragma unroll
-                for (int j = 0; j < V; j++) {
-                    const C c = K::canon(v[k * V + j]);
-                    ltm |= (uint32_t)c_lt(c, piv) << (k * V + j);
-                    gtm |= (uint32_t)c_lt(piv, c) << (k * V + j);
+    if (warp == NW) {
+        // ================================ producer ================================
+        if (lane != 0) return;
+        // element range of the buffer that 16-byte copies may touch
+        const int64_t n = (int64_t)job->n;
+        const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
+        const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
+        uint32_t claim = 0;
+        for (uint32_t it = 0;; it++) {
+            const int s = (int)(it % NBUF);
+            if (it >= (uint32_t)NBUF && !mbar_wait(&empty[s], ((it / NBUF) - 1) & 1u, wait_limit)) {
+                set_status(ctl, TSQS_ETIMEOUT);
+            }
+            TileMeta m;
+            // tiles are claimed two at a time (one atomic per pair); the pair's second
+            // tile is used on the next slot
+            if (job->offset_mode != 0u) {
+                // look-back mode: a claimed tile must start at once (its successors wait
+                // for its aggregate), so claim one at a time
+                m.tile = atomicAdd(&ctl->tile_claim, 1u);
+            } else {
+                if ((it & 1u) == 0u) claim = atomicAdd(&ctl->tile_claim, 2u);
+                m.tile = claim + (it & 1u);
+            }
+            m.valid = 0;
+            m.cs = m.ce = 0;
+            if (m.tile < ntiles) {
+                m.si = job->tile_seg[m.tile];
+                if (m.si < nfront) {
+                    const SegDesc sd = job->front[par][m.si];
+                    m.valid = 1;
+                    m.sb = sd.begin; m.se = sd.end;
+                    m.piv_lo = sd.piv_lo; m.piv_hi = sd.piv_hi;
+                    m.tile_begin = sd.tile_begin; m.ntiles_seg = sd.ntiles;
+                    m.tl = m.tile - sd.tile_begin;
+                    m.t0 = sd.s0 + (int64_t)m.tl * TILE;
+                    // aligned hull of the segment inside the tile, clipped to the buffer
+                    const int64_t a_sb = (int64_t)sd.begin - (((int64_t)sd.begin + job->vec_off) % V);
+                    const int64_t a_se = (int64_t)sd.end + ((V - (((int64_t)sd.end + job->vec_off) % V)) % V);
+                    m.cs = max(max(m.t0, a_sb), e_lo);
+                    m.ce = min(min(m.t0 + TILE, a_se), e_hi);
+                    if (m.ce < m.cs) m.ce = m.cs;
+                } else {
+                    set_status(ctl, TSQS_EINTERNAL);
                 }
             } else {
+                m.tile = 0xFFFFFFFFu;                      // end of work
+            }
+            meta[s] = m;
+            if (m.valid && m.ce > m.cs) {
+                const uint32_t bytes = (uint32_t)((m.ce - m.cs) * (int64_t)sizeof(S));
+                mbar_arrive_tx(&full[s], bytes);
+                tma_load_1d(bufs + (size_t)s * TILE + (m.cs - m.t0), src + m.cs, bytes, &full[s]);
+            } else {
+                mbar_arrive(&full[s]);
+            }
+            if (m.tile == 0xFFFFFFFFu) break;
+        }
+        return;
+    }
+
+    // ================================ consumers ================================
+    for (uint32_t it = 0;; it++) {
+        const int s = (int)(it % NBUF);
+        if (!mbar_wait(&full[s], (it / NBUF) & 1u, wait_limit)) {
+            if (tid == 0) set_status(ctl, TSQS_ETIMEOUT);
+            mbar_wait(&full[s], (it / NBUF) & 1u, wait_limit);   // let any copy land
+        }
+        const TileMeta m = meta[s];
+        if (m.tile == 0xFFFFFFFFu) break;
+        S *buf = bufs + (size_t)s * TILE;
+        if (m.valid) {
+            const C piv = c_from<C>(m.piv_lo, m.piv_hi);
+            const int64_t sb = (int64_t)m.sb, se = (int64_t)m.se;
+            // ---- classify (striped: element k * BLOCK + tid of the tile)
+            S v[ITEMS];
+            uint32_t ltm = 0, gtm = 0;
 #pragma unroll
-                for (int j = 0; j < V; j++) {
-                    const int64_t e = e0 + j;
-                    if (e >= sb && e < se) {
-                        v[k * V + j] = src[e];
-                        const C c = K::canon(v[k * V + j]);
-                        ltm |= (uint32_t)c_lt(c, piv) << (k * V + j);
-                        gtm |= (uint32_t)c_lt(piv, c) << (k * V + j);
-                    }
+            for (int k = 0; k < ITEMS; k++) {
+                const int idx = k * BLOCK + tid;
+                const int64_t e = m.t0 + idx;
+                if (e >= sb && e < se) {
+                    v[k] = (e >= m.cs && e < m.ce) ? buf[idx] : src[e];
+                    const C c = K::canon(v[k]);
+                    ltm |= (uint32_t)c_lt(c, piv) << k;
+                    gtm |= (uint32_t)c_lt(piv, c) << k;
                 }
             }
-        }
-
-        // ---- tile scan of packed counts (#<p in bits 0-15, #>p in bits 16-31)
-        const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);
-        uint32_t inc = cnt;
+            // ---- tile scan of packed counts (#<p low 16 bits, #>p high 16 bits)
+            const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);
+            uint32_t inc = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) sm.wsum[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t ws = lane < NW ? sm.wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) wsum[warp] = inc;
+            consumer_sync<BLOCK>();                      // all reads of buf done, wsum ready
+            const uint32_t ws = lane < NW ? wsum[lane] : 0u;
             uint32_t wi = ws;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += y;
             }
-            if (lane < NW) sm.wsum[lane] = wi - ws;
             const uint32_t total = __shfl_sync(0xffffffffu, wi, NW - 1);
-            const uint64_t agg_lt = total & 0xFFFFu, agg_gt = total >> 16;
-            uint64_t ex_lt = 0, ex_gt = 0;
-            unsigned long long *stw = job->tile_status + tile;
-            // test hook: tile 1 never publishes, so its successors' waits must expire
-            const bool publish = !((job->pad & 2u) && tile == 1u);
-            if (tl == 0) {
-                if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagInc, agg_lt, agg_gt));
-            } else {
-                if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagAgg, agg_lt, agg_gt));
-                lookback(job->tile_status, tile, sd.tile_begin, job->spin_limit, ctl, ex_lt, ex_gt);
-                if (lane == 0 && publish)
-                    st_relaxed(stw, lb_pack(kFlagInc, ex_lt + agg_lt, ex_gt + agg_gt));
-            }
-            if (lane == 0) { sm.ex_lt = ex_lt; sm.ex_gt = ex_gt; sm.tot = total; }
-        }
-        __syncthreads();
-
-        // ---- stage: <p from the front of the tile buffer, >p from its back
-        const uint32_t texcl = sm.wsum[warp] + inc - cnt;
-        uint32_t lp = texcl & 0xFFFFu, gp = texcl >> 16;
+            const uint32_t wex = __shfl_sync(0xffffffffu, wi - ws, warp);
+            const uint32_t texcl = wex + inc - cnt;
+            // ---- atomic mode: thread 0 reserves both runs now, so the atomic's latency
+            // overlaps with the staging below
+            unsigned long long resv = 0ull;
+            if (tid == 0 && job->offset_mode == 0u)
+                resv = atomicAdd(job->seg_cursor + m.si,
+                                 (unsigned long long)(((uint64_t)(total >> 16) << 32) | (total & 0xFFFFu)));
+            // ---- stage into the same buffer: <p from its front, >p from its back
+            uint32_t lp = texcl & 0xFFFFu, gp = texcl >> 16;
 #pragma unroll
-        for (int i = 0; i < ITEMS; i++) {
-            if ((ltm >> i) & 1u) sm.stage[lp++] = v[i];
-            else if ((gtm >> i) & 1u) sm.stage[TILE - 1 - gp++] = v[i];
-        }
-        __syncthreads();
-
-        // ---- coalesced write-out: <p ascending from begin, >p descending from end
-        const uint32_t tlt = sm.tot & 0xFFFFu, tgt = sm.tot >> 16;
-        S *dl = dst + (sd.begin + sm.ex_lt);
-        for (uint32_t i = tid; i < tlt; i += BLOCK) dl[i] = sm.stage[i];
-        S *dr = dst + (sd.end - 1 - sm.ex_gt);
-        for (uint32_t i = tid; i < tgt; i += BLOCK) *(dr - i) = sm.stage[TILE - 1 - i];
-
-        // ---- last tile of the segment: push the children and the =p fill
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t d = atomicAdd(&job->seg_done[si], 1u);
-            sm.last = (d + 1 == sd.ntiles) ? 1u : 0u;
-        }
-        __syncthreads();
-        if (sm.last && epilogue) {
-            if (tid == 0) {
-                __threadfence();
-                const unsigned long long w = ld_relaxed(job->tile_status + sd.tile_begin + sd.ntiles - 1);
-                const uint64_t nlt = (w >> 31) & 0x7FFFFFFFull, ngt = w & 0x7FFFFFFFull;
-                const uint64_t m = sd.end - sd.begin;
-                const int np = par ^ 1;
-                sm.nch = 0;
-                if ((w >> 62) != 2ull || nlt + ngt >= m) {
-                    // p is an element of the segment, so the =p run is never empty; a
-                    // violation means corrupted state: stop instead of looping forever
-                    set_status(ctl, TSQS_EINTERNAL);
+            for (int k = 0; k < ITEMS; k++) {
+                if ((ltm >> k) & 1u) buf[lp++] = v[k];
+                else if ((gtm >> k) & 1u) buf[TILE - 1 - gp++] = v[k];
+            }
+            // ---- warp 0: the tile's offsets in the segment, then count the finished tile
+            if (warp == 0) {
+                const uint64_t agg_lt = total & 0xFFFFu, agg_gt = total >> 16;
+                uint64_t ex_lt = 0, ex_gt = 0;
+                if (job->offset_mode == 0u) {
+                    // one 64-bit atomic reserved both runs: #<p in the low word, #>p high
+                    ex_lt = resv & 0xFFFFFFFFull;
+                    ex_gt = resv >> 32;
                 } else {
-                    push_segment<V, TILE>(job, ctl, np, sd.begin, sd.begin + nlt);
-                    push_segment<V, TILE>(job, ctl, np, sd.end - ngt, sd.end);
-                    sm.eqb = sd.begin + nlt;
-                    sm.eqe = sd.end - ngt;
-                    const uint32_t nch = (uint32_t)((sm.eqe - sm.eqb + kFillChunk - 1) / kFillChunk);
-                    const uint32_t fb = atomicAdd(&ctl->nleaf[np], nch);
-                    if ((uint64_t)fb + nch > job->cap_leaves) set_status(ctl, TSQS_EINTERNAL);
-                    else { sm.nch = nch; sm.fb = fb; }
+                    unsigned long long *stw = job->tile_status + m.tile;
+                    const bool publish = !((job->pad & 2u) && m.tile == 1u);   // test hook
+                    if (m.tl == 0) {
+                        if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagInc, agg_lt, agg_gt));
+                    } else {
+                        if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagAgg, agg_lt, agg_gt));
+                        lookback(job->tile_status, m.tile, m.tile_begin, job->spin_limit, ctl, ex_lt, ex_gt);
+                        if (lane == 0 && publish)
+                            st_relaxed(stw, lb_pack(kFlagInc, ex_lt + agg_lt, ex_gt + agg_gt));
+                    }
+                }
+                if (lane == 0) {
+                    misc->ex_lt = ex_lt;
+                    misc->ex_gt = ex_gt;
+                    misc->total = total;
                 }
             }
-            __syncthreads();
-            const uint32_t nch = sm.nch;
-            for (uint32_t c = tid; c < nch; c += BLOCK) {
-                LeafItem it;
-                it.begin = sm.eqb + (uint64_t)c * kFillChunk;
-                const uint64_t rest = sm.eqe - it.begin;
-                it.len = (uint32_t)(rest < kFillChunk ? rest : kFillChunk);
-                it.kind = LEAF_FILL;
-                it.v_lo = sd.piv_lo;
-                it.v_hi = sd.piv_hi;
-                job->leaves[par ^ 1][sm.fb + c] = it;
-            }
+            consumer_sync<BLOCK>();
+            // ---- coalesced write-out: <p ascending from begin, >p descending from end
+            const uint32_t tlt = misc->total & 0xFFFFu, tgt = misc->total >> 16;
+            S *dl = dst + (m.sb + misc->ex_lt);
+            for (uint32_t i = tid; i < tlt; i += BLOCK) dl[i] = buf[i];
+            S *dr = dst + (m.se - 1 - misc->ex_gt);
+            for (uint32_t i = tid; i < tgt; i += BLOCK) *(dr - i) = buf[TILE - 1 - i];
         }
-        __syncthreads();
+        // ---- hand the buffer back to the producer
+        fence_proxy_async();
+        consumer_sync<BLOCK>();
+        if (tid == 0) mbar_arrive(&empty[s]);
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Leaf pass (persistent): on-chip bitonic sort of small segments and =p fills.
+// Leaf pass (persistent): on-chip sort of small segments and =p fills.
+// A segment of len <= 4096 is padded with the largest canonical key to
+// P = max(32, 2^ceil(log2 len)) and sorted by a bitonic network held in registers:
+// thread t owns elements [t E, t E + E) (E = 16 for P >= 512, else P / 32 in one
+// warp).  Compare-exchanges between elements of one thread run on registers,
+// between lanes of a warp through shuffles, and only strides of 32 E or more go
+// through shared memory.
 // ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned int c_min(unsigned int a, unsigned int b) { return min(a, b); }
+__device__ __forceinline__ unsigned int c_maxv(unsigned int a, unsigned int b) { return max(a, b); }
+__device__ __forceinline__ unsigned long long c_min(unsigned long long a, unsigned long long b) { return min(a, b); }
+__device__ __forceinline__ unsigned long long c_maxv(unsigned long long a, unsigned long long b) { return max(a, b); }
+__device__ __forceinline__ U128 c_min(U128 a, U128 b) { return c_lt(b, a) ? b : a; }
+__device__ __forceinline__ U128 c_maxv(U128 a, U128 b) { return c_lt(b, a) ? a : b; }
+__device__ __forceinline__ unsigned int c_shfl_xor(unsigned int v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ unsigned long long c_shfl_xor(unsigned long long v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ U128 c_shfl_xor(U128 v, int m) {
+    return U128{__shfl_xor_sync(0xffffffffu, v.lo, m), __shfl_xor_sync(0xffffffffu, v.hi, m)};
+}
 
 template <class C>
-__device__ __forceinline__ void bitonic_smem(C *s, uint32_t P, int nthreads) {
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < (P >> 1); i += nthreads) {
-                const uint32_t a = 2 * i - (i & (j - 1));
-                const uint32_t b = a + j;
-                const bool up = (a & k) == 0;
-                const C x = s[a], y = s[b];
-                if (up ? c_lt(y, x) : c_lt(x, y)) { s[a] = y; s[b] = x; }
-            }
-            __syncthreads();
-        }
-    }
+__device__ __forceinline__ void cmpx(C &a, C &b, bool asc) {
+    const C lo = c_min(a, b), hi = c_maxv(a, b);
+    a = asc ? lo : hi;
+    b = asc ? hi : lo;
 }
 
-template <int KIND, int LB>
-__global__ void __launch_bounds__(LB) k_leaf(const Job *__restrict__ job, Ctl *ctl) {
+// Sorts s[0, P) ascending (P a power of two, 32 E <= P <= E * blockDim.x).  Every
+// thread of the block must call it (it contains block barriers).
+// Shared-memory index with one pad word per 32: the blocked layout (stride E) and the
+// cross-warp partners then fall into distinct banks.
+__device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
+
+template <class C, int E>
+__device__ __forceinline__ void bitonic_regs(C *s, uint32_t P) {
+    const uint32_t t = threadIdx.x;
+    const uint32_t NT = P / E;
+    const bool act = t < NT;
+    C v[E];
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E; r++) v[r] = s[pad32(t * E + r)];
+        // merges of width k <= E: all inside the thread
+#pragma unroll
+        for (int k = 2; k <= E; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const int q = r ^ j;
+                    if (q > r) cmpx(v[r], v[q], ((t * E + r) & (uint32_t)k) == 0u);
+                }
+            }
+        }
+    }
+    for (uint32_t k = 2 * E; k <= P; k <<= 1) {
+        const bool asc = ((t * E) & k) == 0u;
+        // strides across warps: through shared memory
+        for (uint32_t j = k >> 1; j >= 32u * E; j >>= 1) {
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+            }
+            __syncthreads();
+            if (act) {
+                const bool keep_min = (((t * E) & j) == 0u) == asc;
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const C w = s[pad32((t * E + r) ^ j)];
+                    v[r] = keep_min ? c_min(v[r], w) : c_maxv(v[r], w);
+                }
+            }
+        }
+        if (act) {
+            // strides across lanes: shuffles
+            const uint32_t jtop = min(k >> 1, 16u * E);
+            for (uint32_t j = jtop; j >= (uint32_t)E; j >>= 1) {
+                const int lm = (int)(j / E);
+                const bool keep_min = ((t & (uint32_t)lm) == 0u) == asc;
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const C w = c_shfl_xor(v[r], lm);
+                    v[r] = keep_min ? c_min(v[r], w) : c_maxv(v[r], w);
+                }
+            }
+            // strides inside the thread
+#pragma unroll
+            for (int j = E >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const int q = r ^ j;
+                    if (q > r) cmpx(v[r], v[q], asc);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+    }
+    __syncthreads();
+}
+
+template <int KIND, int LB, int MINB>
+__global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
+    static_assert(LB * 16 >= kMaxSmall, "block too small for the largest leaf");
     extern __shared__ __align__(16) unsigned char leaf_raw[];
     C *s = reinterpret_cast<C *>(leaf_raw);
     __shared__ uint32_t s_item;
     const int par = ctl->level & 1;
-    if (*(volatile uint32_t *)&ctl->status) return;        // queues may be inconsistent
+    if (block_aborted(ctl)) return;                         // queues may be inconsistent
     const uint32_t nl = min(ctl->nleaf[par], job->cap_leaves);
     const S *src = buffer<K>(job, par);          // may be the same buffer as out
     S *out = reinterpret_cast<S *>(job->base);
@@ -578,13 +798,18 @@ __global__ void __launch_bounds__(LB) k_leaf(const Job *__restrict__ job, Ctl *c
             if (threadIdx.x == 0) set_status(ctl, TSQS_EINTERNAL);
         } else {
             const uint32_t len = it.len;
-            uint32_t P = 1;
+            uint32_t P = 32;
             while (P < len) P <<= 1;
             for (uint32_t i = threadIdx.x; i < P; i += LB)
-                s[i] = i < len ? K::canon(src[it.begin + i]) : c_max<C>();
+                s[pad32(i)] = i < len ? K::canon(src[it.begin + i]) : c_max<C>();
             __syncthreads();
-            bitonic_smem<C>(s, P, LB);
-            for (uint32_t i = threadIdx.x; i < len; i += LB) out[it.begin + i] = K::uncanon(s[i]);
+            // keep every thread busy: E = P / LB elements each once P >= 32 * LB / 8
+            if (P >= 16u * LB) bitonic_regs<C, 16>(s, P);
+            else if (P >= 8u * LB) bitonic_regs<C, 8>(s, P);
+            else if (P >= 4u * LB) bitonic_regs<C, 4>(s, P);
+            else if (P >= 2u * LB) bitonic_regs<C, 2>(s, P);
+            else bitonic_regs<C, 1>(s, P);
+            for (uint32_t i = threadIdx.x; i < len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
             sorted += len;
         }
         __syncthreads();
@@ -617,6 +842,7 @@ __global__ void k_dbg_setup_partition(const Job *__restrict__ job, Ctl *ctl) {
             c_words(K::canon(piv[s]), d.piv_lo, d.piv_hi);
             job->front[0][s] = d;
             job->seg_done[s] = 0u;
+            job->seg_cursor[s] = 0ull;
         }
         __syncthreads();
         for (uint32_t t = threadIdx.x; t < s_nt; t += blockDim.x) {
@@ -642,7 +868,83 @@ __global__ void k_dbg_pivot(const Job *__restrict__ job, Ctl *ctl) {
 
 // Level control (one thread).  Records the level's statistics, resets the consumed
 // queues, advances the level and sets the loop condition.
-__global__ void k_finish(const Job *job, Ctl *ctl, cudaGraphConditionalHandle handle,
-                         int use_handle, uint32_t max_levels);
+__device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGraphConditionalHandle handle,
+                              int use_handle) {
+    const uint32_t L = ctl->level;
+    const int par = L & 1;
+    if (L < (uint32_t)kStatLevels) ctl->level_keys[L] = ctl->front_keys[par];
+    ctl->partition_keys += ctl->front_keys[par];
+    if (ctl->nfront[par] > ctl->max_front) ctl->max_front = ctl->nfront[par];
+    if (ctl->nfront[par]) ctl->levels_done++;
+    ctl->nfront[par] = 0u;
+    ctl->ntiles[par] = 0u;
+    ctl->nleaf[par] = 0u;
+    ctl->front_keys[par] = 0ull;
+    ctl->tile_claim = 0u;
+    ctl->leaf_claim = 0u;
+    ctl->seg_claim = 0u;
+    ctl->level = L + 1;
+    const bool more = (ctl->nfront[par ^ 1] | ctl->nleaf[par ^ 1]) != 0u;
+    if (more && L + 1 >= job->max_levels) set_status(ctl, TSQS_EINTERNAL);
+    const uint32_t cont = (ctl->status == 0u && more) ? 1u : 0u;
+    ctl->cont = cont;
+    if (use_handle) cudaGraphSetConditional(handle, cont);
+}
+
+
+// End of a level: for every segment of the level, read its final (#<p, #>p) and push
+// its children [a, a + #<p) and [b - #>p, b) and the fill of its =p run (the exit and
+// recursion of Section III.F); the last block to finish then runs the level control.
+template <int KIND, int TILE>
+__global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
+                            cudaGraphConditionalHandle handle, int use_handle, uint32_t) {
+    using K = Key<KIND>;
+    __shared__ uint32_t s_last;
+    const int par = ctl->level & 1;
+    const bool ok_state = *(volatile uint32_t *)&ctl->status == 0u;
+    const uint32_t nf = min(ctl->nfront[par], job->cap_front);
+    const int np = par ^ 1;
+    for (uint32_t si = blockIdx.x * blockDim.x + threadIdx.x; ok_state && si < nf;
+         si += gridDim.x * blockDim.x) {
+        const SegDesc sd = job->front[par][si];
+        uint64_t nlt, ngt;
+        const bool ok = seg_totals(job, si, sd.tile_begin, sd.ntiles, nlt, ngt);
+        const uint64_t m = sd.end - sd.begin;
+        if (!ok || nlt + ngt >= m) {
+            // p is an element of the segment, so the =p run is never empty; a violation
+            // means corrupted state: stop instead of looping forever
+            set_status(ctl, TSQS_EINTERNAL);
+            continue;
+        }
+        push_segment<K::V, TILE>(job, ctl, np, sd.begin, sd.begin + nlt);
+        push_segment<K::V, TILE>(job, ctl, np, sd.end - ngt, sd.end);
+        const uint64_t eqb = sd.begin + nlt, eqe = sd.end - ngt;
+        const uint32_t nch = (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
+        const uint32_t fb = atomicAdd(&ctl->nleaf[np], nch);
+        if ((uint64_t)fb + nch > job->cap_leaves) { set_status(ctl, TSQS_EINTERNAL); continue; }
+        for (uint32_t c = 0; c < nch; c++) {
+            LeafItem li;
+            li.begin = eqb + (uint64_t)c * kFillChunk;
+            const uint64_t rest = eqe - li.begin;
+            li.len = (uint32_t)(rest < kFillChunk ? rest : kFillChunk);
+            li.kind = LEAF_FILL;
+            li.v_lo = sd.piv_lo;
+            li.v_hi = sd.piv_hi;
+            job->leaves[np][fb + c] = li;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&ctl->blocks_done, 1u);
+        s_last = (d + 1 == gridDim.x) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        ctl->blocks_done = 0u;
+        level_control(job, ctl, handle, use_handle);
+    }
+}
 
 }  // namespace tsqs

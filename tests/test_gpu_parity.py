@@ -318,3 +318,20 @@ def test_context_stats(T):
     assert st["levels"] >= 10 and st["level_keys"][0] == len(a)
     assert np.array_equal(t.cpu().numpy(), np.sort(a))
     ctx.close()
+
+
+@pytest.mark.parametrize("offset_mode", [0, 1])
+def test_offset_modes_match_oracle(T, orc, offset_mode):
+    """Both ways of placing a tile's runs (per-segment atomic cursor, decoupled
+    look-back) give the oracle's output."""
+    plan = T.Plan()
+    assert T.lib().tsqs_plan_default(1, 0, ctypes.byref(plan)) == 0
+    plan.offset_mode = offset_mode
+    ctx = T.Context(plan)
+    for pattern in ("random", "many_equals", "organ_pipe"):
+        a = int32_pattern(pattern, 2_000_003, seed=offset_mode + 1)
+        t = to_dev(a)
+        T.sort_(t, kind=1, ctx=ctx)
+        assert ctx.status() == 0
+        assert from_dev(t, np.int32).tobytes() == oracle_sort(orc, a, 1).tobytes()
+    ctx.close()
