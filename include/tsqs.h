@@ -61,7 +61,8 @@ typedef enum {
 
 /* Tunables of one sort (the plan the autotuner picks).  Zero fields take defaults. */
 typedef struct {
-    int32_t  tile_items;       /* keys per thread in a partition tile (4-byte keys: 8/16) */
+    int32_t  tile_items;       /* partition kernel shape, 0..3 (0 = default): consumer
+                                  threads x keys per thread x ring depth; see the design doc */
     int32_t  small_threshold;  /* segments of <= this many elements finish on chip (<= 4096) */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
     int32_t  sample_count;     /* pivot sample size: 15, 31 or 63                      */

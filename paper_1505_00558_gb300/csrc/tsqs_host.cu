@@ -37,6 +37,13 @@ const KindOps *get_ops(int kind) {
     return nullptr;
 }
 
+// Partition shape chosen by the plan (tile_items selects one of the compiled shapes).
+const PartVariant &part_of(const KindOps *o, const tsqs_plan &p) {
+    int v = p.tile_items;
+    if (v < 0 || v >= kPartVariants) v = 0;
+    return o->part[v];
+}
+
 size_t kind_size(int kind) {
     const KindOps *o = get_ops(kind);
     return o ? (size_t)o->elem_size : 0;
@@ -81,7 +88,7 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
 
 void fill_default_plan(int key_kind, size_t, tsqs_plan *p) {
     (void)key_kind;
-    p->tile_items = 0;            // fixed per key size in this build
+    p->tile_items = 0;            // partition shape 0 (see KindOps::part)
     p->small_threshold = kMaxSmall;
     p->ctas_per_sm = 0;           // occupancy-derived
     p->sample_count = 31;
@@ -102,6 +109,7 @@ void normalise_plan(tsqs_plan *p) {
     if (p->seed == 0) p->seed = d.seed;
     if (p->ctas_per_sm < 0) p->ctas_per_sm = 0;
     if (p->offset_mode != 1) p->offset_mode = 0;
+    if (p->tile_items < 0 || p->tile_items >= kPartVariants) p->tile_items = 0;
 }
 
 uint32_t g_debug_spin = 0;        // 0 = default
@@ -157,9 +165,12 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     const int k = o->kind;
     if (c->attrs_set[k]) return TSQS_OK;
     CK(cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem));
-    CK(cudaFuncSetAttribute(o->k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, o->part_smem));
+    for (int v = 0; v < kPartVariants; v++)
+        CK(cudaFuncSetAttribute(o->part[v].k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                o->part[v].smem));
+    const PartVariant &pv = part_of(o, c->plan);
     int occ_p = 0, occ_l = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, o->k_partition, o->part_threads, o->part_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pv.k_partition, pv.threads, pv.smem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem));
     if (c->plan.ctas_per_sm > 0) occ_p = std::min(occ_p, c->plan.ctas_per_sm);
     c->part_grid[k] = std::max(1, occ_p) * c->sms;
@@ -200,7 +211,7 @@ int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile) 
 int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t *offs,
              size_t nseg, Job *j) {
     const size_t es = (size_t)o->elem_size;
-    const Layout L = make_layout(n, nseg, es, c->plan, o->tile);
+    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile);
     if (L.total > c->scratch_bytes) return TSQS_EINTERNAL;
     memset(j, 0, sizeof(*j));
     const uintptr_t b = (uintptr_t)base;
@@ -230,6 +241,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
     j->max_levels = 256u + 8u * lg;
     j->offset_mode = (c->plan.offset_mode == 1 || g_debug_withhold) ? 1u : 0u;
+    j->tile = (uint32_t)part_of(o, c->plan).tile;
     j->seed = c->plan.seed;
     return TSQS_OK;
 }
@@ -277,10 +289,11 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_piv, body, &n_leaf, 1, &kp));
     kp = cudaKernelNodeParams{};
-    kp.func = (void *)o->k_partition;
+    const PartVariant &pv = part_of(o, c->plan);
+    kp.func = (void *)pv.k_partition;
     kp.gridDim = dim3(c->part_grid[k]);
-    kp.blockDim = dim3(o->part_threads);
-    kp.sharedMemBytes = (unsigned)o->part_smem;
+    kp.blockDim = dim3(pv.threads);
+    kp.sharedMemBytes = (unsigned)pv.smem;
     kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_part, body, &n_piv, 1, &kp));
     int use_h = 1;
@@ -322,7 +335,7 @@ int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t n
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, o->tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, part_of(o, c->plan).tile))) return rc;
     if ((rc = ctx_build_graph(c, o))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, n, offs, nseg, &j))) return rc;
@@ -435,7 +448,7 @@ int tsqs_ctx_reserve(tsqs_ctx *c, size_t nmemb_total, size_t nseg, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     int rc = ctx_init_device(c);
     if (rc) return rc;
-    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, o->tile);
+    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, part_of(o, c->plan).tile);
 }
 
 size_t tsqs_ctx_scratch_bytes(const tsqs_ctx *c) { return c ? c->scratch_bytes : 0; }
@@ -448,7 +461,7 @@ size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
     tsqs_plan p;
     if (plan) p = *plan; else fill_default_plan(kind, nmemb_total, &p);
     normalise_plan(&p);
-    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, o->tile).total;
+    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, part_of(o, p).tile).total;
 }
 
 int tsqs_ctx_device_status(tsqs_ctx *c, void *stream) {
@@ -561,7 +574,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, o->tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, nmemb, nullptr, 0, &j))) return rc;
     if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
@@ -585,8 +598,9 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
         CK(cudaEventRecord(ev[3], s));
         CK(cudaLaunchKernel(o->k_pivot, dim3(c->sms * 4), dim3(o->pivot_block), args2, 0, s));
         CK(cudaEventRecord(ev[0], s));
-        CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[k]), dim3(o->part_threads), args2,
-                            (size_t)o->part_smem, s));
+        const PartVariant &pv = part_of(o, c->plan);
+        CK(cudaLaunchKernel(pv.k_partition, dim3(c->part_grid[k]), dim3(pv.threads), args2,
+                            (size_t)pv.smem, s));
         CK(cudaEventRecord(ev[1], s));
         CK(cudaLaunchKernel(o->k_finish, dim3(c->sms), dim3(128), argsf, 0, s));
         CK(cudaMemcpyAsync(c->h_cont, &c->d_ctl->cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -630,10 +644,10 @@ int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_k
     const KindOps *o = get_ops(key_kind);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, o->tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)base, nmemb, nullptr, 0, &j))) return rc;
-    const Layout L = make_layout(nmemb, 1, elem_size, c->plan, o->tile);
+    const Layout L = make_layout(nmemb, 1, elem_size, c->plan, part_of(o, c->plan).tile);
     char *misc = c->scratch + L.misc_off;
     uint64_t *d_offs = (uint64_t *)misc;
     uint64_t *d_pos = (uint64_t *)(misc + 64);
@@ -677,7 +691,7 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, o->tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, part_of(o, c->plan).tile))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)src, nmemb, d_seg_offsets, nseg, &j))) return rc;
     j.alt = dst;
@@ -690,8 +704,9 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     void *args2[] = {&pj, &pc};
     const unsigned gs = (unsigned)std::min<size_t>(nseg, (size_t)c->sms * 8);
     CK(cudaLaunchKernel(o->k_dbg_setup_partition, dim3(gs), dim3(256), args2, 0, s));
-    CK(cudaLaunchKernel(o->k_partition, dim3(c->part_grid[key_kind]), dim3(o->part_threads), args2,
-                        (size_t)o->part_smem, s));
+    const PartVariant &pv = part_of(o, c->plan);
+    CK(cudaLaunchKernel(pv.k_partition, dim3(c->part_grid[key_kind]), dim3(pv.threads), args2,
+                        (size_t)pv.smem, s));
     CK(cudaLaunchKernel(o->k_dbg_counts, dim3(c->sms), dim3(256), args2, 0, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaEventRecord(c->done_ev, s));

@@ -80,6 +80,8 @@ struct Job {
                               // the bounded wait)
     uint32_t max_levels;      // level cap; exceeding it stops the loop with an error
     uint32_t offset_mode;     // 0: per-segment atomic cursor, 1: decoupled look-back
+    uint32_t tile;            // keys per partition tile of the partition kernel in use
+    uint32_t pad3;
     uint64_t seed;            // sample jitter seed
     // step-level test hooks
     const void *dbg_pivots;   // debug partition: pivots of the given segments
@@ -88,16 +90,24 @@ struct Job {
     void *dbg_pivot_out;      // debug pivot: chosen pivot (original representation)
 };
 
+// One compiled shape of the partition kernel.
+struct PartVariant {
+    const void *k_partition;
+    int tile;                 // keys per tile
+    int threads;              // consumer warps + one producer warp
+    int smem;                 // dynamic shared memory
+    int nbuf;                 // depth of the shared-memory ring
+};
+constexpr int kPartVariants = 4;
+
 // Kernel entry points of one key kind (filled by the per-kind translation units).
 struct KindOps {
     int kind;
     int elem_size;
-    int tile;                 // keys per partition tile
-    int part_block, leaf_block, pivot_block;
-    int part_threads;         // consumer warps + one producer warp
-    int part_smem;            // dynamic shared memory of the partition kernel
+    int leaf_block, pivot_block;
     int leaf_smem;            // dynamic shared memory of the leaf kernel
-    const void *k_init, *k_leaf, *k_pivot, *k_partition, *k_finish;
+    PartVariant part[kPartVariants];   // [0] is the default shape
+    const void *k_init, *k_leaf, *k_pivot, *k_finish;
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
 };
 

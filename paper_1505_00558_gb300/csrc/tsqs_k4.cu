@@ -4,27 +4,36 @@
 namespace tsqs {
 
 namespace {
-constexpr int kPartBlock = 256, kItems = 16, kTile = kPartBlock * kItems;
-constexpr int kLeafBlock = 256, kPivotBlock = 256, kNBuf = 3;
+constexpr int kLeafBlock = 256, kPivotBlock = 256;
+
+template <int KIND, int BLOCK, int ITEMS, int NBUF>
+PartVariant part_variant() {
+    PartVariant v;
+    v.k_partition = (const void *)k_partition<KIND, BLOCK, ITEMS, NBUF>;
+    v.tile = BLOCK * ITEMS;
+    v.threads = BLOCK + 32;
+    v.smem = (int)PartLayout<KIND, BLOCK, ITEMS, NBUF>::bytes;
+    v.nbuf = NBUF;
+    return v;
+}
 
 template <int KIND>
 KindOps make_ops() {
     KindOps o{};
     o.kind = KIND;
     o.elem_size = 4;
-    o.tile = kTile;
-    o.part_block = kPartBlock;
-    o.part_threads = kPartBlock + 32;
-    o.part_smem = (int)PartLayout<KIND, kPartBlock, kItems, kNBuf>::bytes;
     o.leaf_block = kLeafBlock;
     o.pivot_block = kPivotBlock;
     o.leaf_smem = (kMaxSmall + kMaxSmall / 32) * (int)sizeof(typename Key<KIND>::C);
-    o.k_init = (const void *)k_init<KIND, kTile>;
+    o.part[0] = part_variant<KIND, 256, 16, 3>();
+    o.part[1] = part_variant<KIND, 256, 16, 4>();
+    o.part[2] = part_variant<KIND, 512, 16, 2>();
+    o.part[3] = part_variant<KIND, 128, 16, 4>();
+    o.k_init = (const void *)k_init<KIND>;
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, 3>;
-    o.k_pivot = (const void *)k_pivot<KIND, kTile>;
-    o.k_partition = (const void *)k_partition<KIND, kPartBlock, kItems, kNBuf>;
-    o.k_finish = (const void *)k_level_end<KIND, kTile>;
-    o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND, kTile>;
+    o.k_pivot = (const void *)k_pivot<KIND>;
+    o.k_finish = (const void *)k_level_end<KIND>;
+    o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;
     o.k_dbg_counts = (const void *)k_dbg_counts;
     o.k_dbg_pivot = (const void *)k_dbg_pivot<KIND>;
     return o;

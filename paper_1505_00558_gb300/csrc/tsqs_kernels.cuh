@@ -38,15 +38,21 @@ struct __align__(16) Rec16 { unsigned long long key, pay; };
 
 template <int KIND> struct Key;
 
+// D is the domain the partition compares in: the native signed/unsigned integer
+// where the hardware orders it directly, the canonical form otherwise.
 template <> struct Key<TSQS_I32> {
-    using S = unsigned int; using C = unsigned int; static constexpr int V = 4;
+    using S = unsigned int; using C = unsigned int; using D = int; static constexpr int V = 4;
     static __device__ __forceinline__ C canon(S x) { return x ^ 0x80000000u; }
     static __device__ __forceinline__ S uncanon(C c) { return c ^ 0x80000000u; }
+    static __device__ __forceinline__ D dom(S x) { return (int)x; }
+    static __device__ __forceinline__ D pdom(C c) { return (int)(c ^ 0x80000000u); }
 };
 template <> struct Key<TSQS_U32> {
-    using S = unsigned int; using C = unsigned int; static constexpr int V = 4;
+    using S = unsigned int; using C = unsigned int; using D = unsigned int; static constexpr int V = 4;
     static __device__ __forceinline__ C canon(S x) { return x; }
     static __device__ __forceinline__ S uncanon(C c) { return c; }
+    static __device__ __forceinline__ D dom(S x) { return x; }
+    static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 template <> struct Key<TSQS_F32> {
     using S = unsigned int; using C = unsigned int; static constexpr int V = 4;
@@ -56,16 +62,23 @@ template <> struct Key<TSQS_F32> {
     static __device__ __forceinline__ S uncanon(C c) {
         return c ^ (~(unsigned int)((int)c >> 31) | 0x80000000u);
     }
+    using D = unsigned int;
+    static __device__ __forceinline__ D dom(S x) { return canon(x); }
+    static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 template <> struct Key<TSQS_I64> {
-    using S = unsigned long long; using C = unsigned long long; static constexpr int V = 2;
+    using S = unsigned long long; using C = unsigned long long; using D = long long; static constexpr int V = 2;
     static __device__ __forceinline__ C canon(S x) { return x ^ 0x8000000000000000ull; }
     static __device__ __forceinline__ S uncanon(C c) { return c ^ 0x8000000000000000ull; }
+    static __device__ __forceinline__ D dom(S x) { return (long long)x; }
+    static __device__ __forceinline__ D pdom(C c) { return (long long)(c ^ 0x8000000000000000ull); }
 };
 template <> struct Key<TSQS_U64> {
-    using S = unsigned long long; using C = unsigned long long; static constexpr int V = 2;
+    using S = unsigned long long; using C = unsigned long long; using D = unsigned long long; static constexpr int V = 2;
     static __device__ __forceinline__ C canon(S x) { return x; }
     static __device__ __forceinline__ S uncanon(C c) { return c; }
+    static __device__ __forceinline__ D dom(S x) { return x; }
+    static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 template <> struct Key<TSQS_F64> {
     using S = unsigned long long; using C = unsigned long long; static constexpr int V = 2;
@@ -75,14 +88,22 @@ template <> struct Key<TSQS_F64> {
     static __device__ __forceinline__ S uncanon(C c) {
         return c ^ (~(unsigned long long)((long long)c >> 63) | 0x8000000000000000ull);
     }
+    using D = unsigned long long;
+    static __device__ __forceinline__ D dom(S x) { return canon(x); }
+    static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 template <> struct Key<TSQS_U64_U64_REC> {
     using S = Rec16; using C = U128; static constexpr int V = 1;
     static __device__ __forceinline__ C canon(S x) { return U128{x.pay, x.key}; }
     static __device__ __forceinline__ S uncanon(C c) { Rec16 r; r.key = c.hi; r.pay = c.lo; return r; }
+    using D = U128;
+    static __device__ __forceinline__ D dom(S x) { return canon(x); }
+    static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 
-// canonical-order helpers, overloaded on C
+// canonical-order helpers, overloaded on C (and on the comparison domains D)
+__device__ __forceinline__ bool c_lt(int a, int b) { return a < b; }
+__device__ __forceinline__ bool c_lt(long long a, long long b) { return a < b; }
 __device__ __forceinline__ bool c_lt(unsigned int a, unsigned int b) { return a < b; }
 __device__ __forceinline__ bool c_lt(unsigned long long a, unsigned long long b) { return a < b; }
 __device__ __forceinline__ bool c_lt(U128 a, U128 b) {
@@ -119,6 +140,46 @@ __device__ __forceinline__ void load_vec(const S *p, S *out) {
     u.q = q;
 #pragma unroll
     for (int j = 0; j < V; j++) out[j] = u.s[j];
+}
+
+// 16-byte shared-memory load of V storage elements (address 16-byte aligned).
+template <class S, int V>
+__device__ __forceinline__ void lds_vec(const S *p, S *out) {
+    union { uint4 q; S s[V]; } u;
+    u.q = *reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int j = 0; j < V; j++) out[j] = u.s[j];
+}
+// 16-byte global store of V storage elements (address 16-byte aligned).
+template <class S, int V>
+__device__ __forceinline__ void stg_vec(S *p, const S *in) {
+    union { uint4 q; S s[V]; } u;
+#pragma unroll
+    for (int j = 0; j < V; j++) u.s[j] = in[j];
+    *reinterpret_cast<uint4 *>(p) = u.q;
+}
+
+// Copies cnt staged elements st[0, cnt) to dst[x, x + cnt): scalar up to the first
+// 16-byte boundary of the destination, 16-byte stores for the body, scalar tail.
+// (element x of dst is 16-byte aligned iff (x + vec_off) % V == 0)
+template <class S, int V, int NT>
+__device__ __forceinline__ void copy_run(S *__restrict__ dst, uint64_t x, const S *st,
+                                         uint32_t cnt, uint32_t vec_off) {
+    if (cnt == 0) return;
+    uint32_t head = (uint32_t)((V - ((x + vec_off) % V)) % V);
+    if (head > cnt) head = cnt;
+    const uint32_t nvec = (cnt - head) / V;
+    const uint32_t body_end = head + nvec * V;
+    const int t = threadIdx.x;
+    if ((uint32_t)t < head) dst[x + t] = st[t];
+    for (uint32_t q = t; q < nvec; q += NT) {
+        S tmp[V];
+#pragma unroll
+        for (int j = 0; j < V; j++) tmp[j] = st[head + q * V + j];
+        stg_vec<S, V>(dst + x + head + q * V, tmp);
+    }
+    const uint32_t tail = cnt - body_end;
+    if ((uint32_t)t < tail) dst[x + body_end + t] = st[body_end + t];
 }
 
 // ---------------------------------------------------------------------------------
@@ -192,8 +253,9 @@ __device__ __forceinline__ bool seg_totals(const Job *job, uint32_t si, uint32_t
 }
 
 // Pushes [b, e) to the next level: frontier if larger than small_T, leaf otherwise.
-template <int V, int TILE>
+template <int V>
 __device__ void push_segment(const Job *job, Ctl *ctl, int np, uint64_t b, uint64_t e) {
+    const int TILE = (int)job->tile;
     if (e <= b) return;
     const uint64_t m = e - b;
     if (m > job->small_T) {
@@ -228,7 +290,7 @@ __global__ void k_setup(Job *job, Ctl *ctl, Job j);
 
 // Seeds level 0: one segment [0, n) or every segment of seg_offsets.  Segments of 0 or
 // 1 element are already in place; small ones go straight to the leaf queue.
-template <int KIND, int TILE>
+template <int KIND>
 __global__ void k_init(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
@@ -238,7 +300,7 @@ __global__ void k_init(const Job *__restrict__ job, Ctl *ctl) {
         const uint64_t e = job->seg_offsets ? job->seg_offsets[s + 1] : job->n;
         if (e < b || e > job->n || e - b >= (1ull << 31)) { set_status(ctl, TSQS_EINVAL); continue; }
         if (e - b <= 1) continue;
-        push_segment<K::V, TILE>(job, ctl, 0, b, e);
+        push_segment<K::V>(job, ctl, 0, b, e);
     }
 }
 
@@ -302,7 +364,7 @@ __device__ typename K::C sample_pivot(const typename K::S *src, uint64_t b, uint
 }
 
 // One block per frontier segment (grid-stride): pivot by warp 0, tile tables by all.
-template <int KIND, int TILE>
+template <int KIND>
 __global__ void k_pivot(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     const int par = ctl->level & 1;
@@ -456,11 +518,14 @@ struct PartLayout {
     using S = typename Key<KIND>::S;
     static constexpr int TILE = BLOCK * ITEMS;
     static constexpr int NW = BLOCK / 32;
-    static constexpr size_t buf_bytes = (size_t)TILE * sizeof(S);
+    // one ring slot: the tile plus one 16-byte dummy slot that absorbs =p elements
+    static constexpr int SLOT = TILE + Key<KIND>::V;
+    static constexpr size_t buf_bytes = (size_t)SLOT * sizeof(S);
     static constexpr size_t off_bar = NBUF * buf_bytes;
     static constexpr size_t off_meta = off_bar + 2 * NBUF * sizeof(unsigned long long);
     static constexpr size_t off_misc = off_meta + NBUF * sizeof(TileMeta);
     static constexpr size_t bytes = off_misc + 128 + NW * sizeof(uint32_t);
+    static_assert(2 * 24 <= 128, "misc area");
 };
 
 struct PartMisc {
@@ -469,12 +534,14 @@ struct PartMisc {
 };
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
-__global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restrict__ job, Ctl *ctl) {
+__global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 8))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
     using LY = PartLayout<KIND, BLOCK, ITEMS, NBUF>;
-    constexpr int TILE = LY::TILE, V = K::V, NW = LY::NW;
+    using D = typename K::D;
+    constexpr int TILE = LY::TILE, V = K::V, NW = LY::NW, SLOT = LY::SLOT, NV = ITEMS / V;
+    static_assert(ITEMS % V == 0, "whole 16-byte vectors per thread");
     static_assert(ITEMS <= 32 && TILE < 65536 && (TILE % V) == 0, "tile shape");
     extern __shared__ __align__(128) unsigned char psm[];
     S *bufs = reinterpret_cast<S *>(psm);
@@ -551,7 +618,7 @@ __global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restri
             if (m.valid && m.ce > m.cs) {
                 const uint32_t bytes = (uint32_t)((m.ce - m.cs) * (int64_t)sizeof(S));
                 mbar_arrive_tx(&full[s], bytes);
-                tma_load_1d(bufs + (size_t)s * TILE + (m.cs - m.t0), src + m.cs, bytes, &full[s]);
+                tma_load_1d(bufs + (size_t)s * SLOT + (m.cs - m.t0), src + m.cs, bytes, &full[s]);
             } else {
                 mbar_arrive(&full[s]);
             }
@@ -561,6 +628,14 @@ __global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restri
     }
 
     // ================================ consumers ================================
+    // Two-stage software pipeline over this CTA's tiles: phase A of tile i (classify,
+    // scan, stage in place, reserve the output runs) runs before phase B of tile i-1
+    // (write-out), so the reservation's round trip overlaps with the next tile's work.
+    bool have_prev = false;
+    int prev_slot = 0;
+    uint64_t prev_sb = 0, prev_se = 0;
+    unsigned long long prev_resv = 0ull;   // packed (ex_gt << 32 | ex_lt), thread 0
+    uint32_t prev_total = 0;               // packed (tgt << 16 | tlt), thread 0
     for (uint32_t it = 0;; it++) {
         const int s = (int)(it % NBUF);
         if (!mbar_wait(&full[s], (it / NBUF) & 1u, wait_limit)) {
@@ -568,35 +643,63 @@ __global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restri
             mbar_wait(&full[s], (it / NBUF) & 1u, wait_limit);   // let any copy land
         }
         const TileMeta m = meta[s];
-        if (m.tile == 0xFFFFFFFFu) break;
-        S *buf = bufs + (size_t)s * TILE;
-        if (m.valid) {
-            const C piv = c_from<C>(m.piv_lo, m.piv_hi);
+        const bool end = m.tile == 0xFFFFFFFFu;
+        const bool work = !end && m.valid;
+        S *buf = bufs + (size_t)s * SLOT;
+
+        // ---- phase A, part 1: classify.  Thread t holds the 16-byte vectors
+        // k * BLOCK + t of the tile (k < NV), i.e. elements (k * BLOCK + t) * V + j.
+        S v[ITEMS];
+        uint32_t ltm = 0, gtm = 0;
+        if (work) {
+            const D pd = K::pdom(c_from<C>(m.piv_lo, m.piv_hi));
             const int64_t sb = (int64_t)m.sb, se = (int64_t)m.se;
-            // ---- classify (striped: element k * BLOCK + tid of the tile)
-            S v[ITEMS];
-            uint32_t ltm = 0, gtm = 0;
+            const bool full_tile = m.t0 >= sb && m.t0 + TILE <= se && m.cs == m.t0 && m.ce == m.t0 + TILE;
+            if (full_tile) {                             // interior tile: no bounds checks
 #pragma unroll
-            for (int k = 0; k < ITEMS; k++) {
-                const int idx = k * BLOCK + tid;
-                const int64_t e = m.t0 + idx;
-                if (e >= sb && e < se) {
-                    v[k] = (e >= m.cs && e < m.ce) ? buf[idx] : src[e];
-                    const C c = K::canon(v[k]);
-                    ltm |= (uint32_t)c_lt(c, piv) << k;
-                    gtm |= (uint32_t)c_lt(piv, c) << k;
+                for (int k = 0; k < NV; k++) lds_vec<S, V>(buf + (k * BLOCK + tid) * V, &v[k * V]);
+#pragma unroll
+                for (int i = 0; i < ITEMS; i++) {
+                    const D d = K::dom(v[i]);
+                    ltm |= (uint32_t)c_lt(d, pd) << i;
+                    gtm |= (uint32_t)c_lt(pd, d) << i;
+                }
+            } else {                                     // segment ends or buffer ends
+#pragma unroll
+                for (int k = 0; k < NV; k++) {
+#pragma unroll
+                    for (int j = 0; j < V; j++) {
+                        const int idx = (k * BLOCK + tid) * V + j;
+                        const int64_t e = m.t0 + idx;
+                        if (e >= sb && e < se) {
+                            v[k * V + j] = (e >= m.cs && e < m.ce) ? buf[idx] : src[e];
+                            const D d = K::dom(v[k * V + j]);
+                            ltm |= (uint32_t)c_lt(d, pd) << (k * V + j);
+                            gtm |= (uint32_t)c_lt(pd, d) << (k * V + j);
+                        }
+                    }
                 }
             }
-            // ---- tile scan of packed counts (#<p low 16 bits, #>p high 16 bits)
-            const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);
-            uint32_t inc = cnt;
+        }
+        const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);
+        uint32_t inc = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31) wsum[warp] = inc;
-            consumer_sync<BLOCK>();                      // all reads of buf done, wsum ready
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        if (tid == 0 && have_prev) {                     // the previous tile's offsets
+            misc[(it - 1) & 1u].ex_lt = prev_resv & 0xFFFFFFFFull;
+            misc[(it - 1) & 1u].ex_gt = prev_resv >> 32;
+            misc[(it - 1) & 1u].total = prev_total;
+        }
+        consumer_sync<BLOCK>();        // reads of buf done; wsum and misc[it-1] ready
+
+        // ---- phase A, part 2: block offsets, reservation, staging
+        unsigned long long resv = 0ull;
+        uint32_t total = 0;
+        if (work) {
             const uint32_t ws = lane < NW ? wsum[lane] : 0u;
             uint32_t wi = ws;
 #pragma unroll
@@ -604,60 +707,65 @@ __global__ void __launch_bounds__(BLOCK + 32, 4) k_partition(const Job *__restri
                 const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += y;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, wi, NW - 1);
+            total = __shfl_sync(0xffffffffu, wi, NW - 1);
             const uint32_t wex = __shfl_sync(0xffffffffu, wi - ws, warp);
             const uint32_t texcl = wex + inc - cnt;
-            // ---- atomic mode: thread 0 reserves both runs now, so the atomic's latency
-            // overlaps with the staging below
-            unsigned long long resv = 0ull;
+            const uint64_t agg_lt = total & 0xFFFFu, agg_gt = total >> 16;
+            // atomic mode: one 64-bit atomic on the segment's cursor reserves both runs
+            // (#<p in the low word, #>p in the high word); its result is used one tile
+            // later
             if (tid == 0 && job->offset_mode == 0u)
-                resv = atomicAdd(job->seg_cursor + m.si,
-                                 (unsigned long long)(((uint64_t)(total >> 16) << 32) | (total & 0xFFFFu)));
-            // ---- stage into the same buffer: <p from its front, >p from its back
-            uint32_t lp = texcl & 0xFFFFu, gp = texcl >> 16;
+                resv = atomicAdd(job->seg_cursor + m.si, (unsigned long long)((agg_gt << 32) | agg_lt));
+            // stage without branches: <p from the front, >p from the back, =p (and
+            // elements outside the segment) into the dummy slot at TILE
+            uint32_t lp = texcl & 0xFFFFu, gp = (TILE - 1) - (texcl >> 16);
 #pragma unroll
             for (int k = 0; k < ITEMS; k++) {
-                if ((ltm >> k) & 1u) buf[lp++] = v[k];
-                else if ((gtm >> k) & 1u) buf[TILE - 1 - gp++] = v[k];
+                const uint32_t l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
+                buf[l ? lp : (g ? gp : (uint32_t)TILE)] = v[k];
+                lp += l;
+                gp -= g;
             }
-            // ---- warp 0: the tile's offsets in the segment, then count the finished tile
-            if (warp == 0) {
-                const uint64_t agg_lt = total & 0xFFFFu, agg_gt = total >> 16;
+            if (warp == 0 && job->offset_mode != 0u) {
+                // look-back mode: publish the aggregate, walk back, publish the inclusive
                 uint64_t ex_lt = 0, ex_gt = 0;
-                if (job->offset_mode == 0u) {
-                    // one 64-bit atomic reserved both runs: #<p in the low word, #>p high
-                    ex_lt = resv & 0xFFFFFFFFull;
-                    ex_gt = resv >> 32;
+                unsigned long long *stw = job->tile_status + m.tile;
+                const bool publish = !((job->pad & 2u) && m.tile == 1u);   // test hook
+                if (m.tl == 0) {
+                    if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagInc, agg_lt, agg_gt));
                 } else {
-                    unsigned long long *stw = job->tile_status + m.tile;
-                    const bool publish = !((job->pad & 2u) && m.tile == 1u);   // test hook
-                    if (m.tl == 0) {
-                        if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagInc, agg_lt, agg_gt));
-                    } else {
-                        if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagAgg, agg_lt, agg_gt));
-                        lookback(job->tile_status, m.tile, m.tile_begin, job->spin_limit, ctl, ex_lt, ex_gt);
-                        if (lane == 0 && publish)
-                            st_relaxed(stw, lb_pack(kFlagInc, ex_lt + agg_lt, ex_gt + agg_gt));
-                    }
+                    if (lane == 0 && publish) st_relaxed(stw, lb_pack(kFlagAgg, agg_lt, agg_gt));
+                    lookback(job->tile_status, m.tile, m.tile_begin, job->spin_limit, ctl, ex_lt, ex_gt);
+                    if (lane == 0 && publish)
+                        st_relaxed(stw, lb_pack(kFlagInc, ex_lt + agg_lt, ex_gt + agg_gt));
                 }
-                if (lane == 0) {
-                    misc->ex_lt = ex_lt;
-                    misc->ex_gt = ex_gt;
-                    misc->total = total;
-                }
+                resv = (unsigned long long)((ex_gt << 32) | ex_lt);
             }
-            consumer_sync<BLOCK>();
-            // ---- coalesced write-out: <p ascending from begin, >p descending from end
-            const uint32_t tlt = misc->total & 0xFFFFu, tgt = misc->total >> 16;
-            S *dl = dst + (m.sb + misc->ex_lt);
-            for (uint32_t i = tid; i < tlt; i += BLOCK) dl[i] = buf[i];
-            S *dr = dst + (m.se - 1 - misc->ex_gt);
-            for (uint32_t i = tid; i < tgt; i += BLOCK) *(dr - i) = buf[TILE - 1 - i];
         }
-        // ---- hand the buffer back to the producer
+
+        // ---- phase B of the previous tile: coalesced write-out of both runs
+        if (have_prev) {
+            const PartMisc &pm = misc[(it - 1) & 1u];
+            const S *pbuf = bufs + (size_t)prev_slot * SLOT;
+            const uint32_t tlt = pm.total & 0xFFFFu, tgt = pm.total >> 16;
+            // <p run: staged [0, tlt) -> dst[sb + ex_lt, +tlt); >p run: staged
+            // [TILE - tgt, TILE) -> dst[se - ex_gt - tgt, se - ex_gt), both ascending
+            copy_run<S, V, BLOCK>(dst, prev_sb + pm.ex_lt, pbuf, tlt, job->vec_off);
+            copy_run<S, V, BLOCK>(dst, prev_se - pm.ex_gt - tgt, pbuf + (TILE - tgt), tgt, job->vec_off);
+        }
         fence_proxy_async();
-        consumer_sync<BLOCK>();
-        if (tid == 0) mbar_arrive(&empty[s]);
+        consumer_sync<BLOCK>();        // previous buffer fully read, this tile staged
+        if (tid == 0) {
+            if (have_prev) mbar_arrive(&empty[prev_slot]);
+            if (!work && !end) mbar_arrive(&empty[s]);   // a skipped tile frees its slot now
+        }
+        if (end) break;
+        have_prev = work;
+        prev_slot = s;
+        prev_sb = m.sb;
+        prev_se = m.se;
+        prev_resv = resv;
+        prev_total = total;
     }
 }
 
@@ -826,7 +934,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
 // ---------------------------------------------------------------------------------
 
 // Frontier[0] <- the given segments with the given pivots (original representation).
-template <int KIND, int TILE>
+template <int KIND>
 __global__ void k_dbg_setup_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     const typename K::S *piv = reinterpret_cast<const typename K::S *>(job->dbg_pivots);
@@ -835,7 +943,7 @@ __global__ void k_dbg_setup_partition(const Job *__restrict__ job, Ctl *ctl) {
         const uint64_t b = job->seg_offsets[s], e = job->seg_offsets[s + 1];
         const int64_t s0 = tile_origin<K::V>(b, job->vec_off);
         if (threadIdx.x == 0) {
-            s_nt = e > b ? tiles_for(e, s0, TILE) : 0u;
+            s_nt = e > b ? tiles_for(e, s0, (int)job->tile) : 0u;
             s_tb = atomicAdd(&ctl->ntiles[0], s_nt);
             SegDesc d;
             d.begin = b; d.end = e; d.s0 = s0; d.tile_begin = s_tb; d.ntiles = s_nt;
@@ -895,7 +1003,7 @@ __device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGrap
 // End of a level: for every segment of the level, read its final (#<p, #>p) and push
 // its children [a, a + #<p) and [b - #>p, b) and the fill of its =p run (the exit and
 // recursion of Section III.F); the last block to finish then runs the level control.
-template <int KIND, int TILE>
+template <int KIND>
 __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
                             cudaGraphConditionalHandle handle, int use_handle, uint32_t) {
     using K = Key<KIND>;
@@ -916,8 +1024,8 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
             set_status(ctl, TSQS_EINTERNAL);
             continue;
         }
-        push_segment<K::V, TILE>(job, ctl, np, sd.begin, sd.begin + nlt);
-        push_segment<K::V, TILE>(job, ctl, np, sd.end - ngt, sd.end);
+        push_segment<K::V>(job, ctl, np, sd.begin, sd.begin + nlt);
+        push_segment<K::V>(job, ctl, np, sd.end - ngt, sd.end);
         const uint64_t eqb = sd.begin + nlt, eqe = sd.end - ngt;
         const uint32_t nch = (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
         const uint32_t fb = atomicAdd(&ctl->nleaf[np], nch);
