@@ -386,8 +386,250 @@ def gpu_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def _time_fresh(torch, T, src, kind, reps, records=False, ctx=None):
+    """Median / best ms of sorting fresh copies of src (copy outside the events)."""
+    ts = []
+    for r in range(reps + 2):
+        w = src.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        T.sort_(w, kind=kind, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= 2:
+            ts.append(e0.elapsed_time(e1))
+    status = T.last_device_status() if ctx is None else ctx.status()
+    ok = status == 0
+    return statistics.median(ts), min(ts), ok, w
+
+
+def _line(args, dist, value, config, extra, higher=True, unit=UNIT, ms=None):
+    d = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": dist.world,
+         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+         "higher_is_better": higher, "scaling": "weak", "vs_baseline": None,
+         "dtype": config.pop("dtype", "int32"), "data": "synthetic", "config": config}
+    d.update(extra)
+    if dist.rank == 0:
+        print(json.dumps(d), flush=True)
+
+
 def other_workload(args, dist):
-    raise SystemExit(f"workload {args.workload} is not wired into bench.py yet")
+    import torch
+    torch.cuda.set_device(dist.local)
+    import paper_1505_00558_gb300 as T
+    from workloads import (PATTERNS, int32_pattern, records_u64, floats_normal_specials)
+    T.lib()
+    hbm, hbm_src = peaks()
+    w = args.workload
+    if w == "c1":
+        n = 1_000_000
+        src = torch.from_numpy(int32_pattern("random", n, seed=1)).cuda()
+        med, best, ok, out = _time_fresh(torch, T, src, T.TSQS_I32, max(args.steps, 10))
+        _line(args, dist, n / med / 1e3, {"workload": "1e6 int32 uniform random seed 1 (L2-resident)",
+                                          "n": n}, {"latency_ms_median": med, "latency_ms_best": best,
+                                                    "sorted": ok}, ms=med)
+    elif w == "patterns":
+        n = args.n
+        res = {}
+        pm = p_min(n)
+        for p in PATTERNS:
+            src = torch.from_numpy(int32_pattern(p, n, seed=1)).cuda()
+            med, best, ok, out = _time_fresh(torch, T, src, T.TSQS_I32, 3)
+            ok = ok and bool((out[1:] >= out[:-1]).all().item())
+            res[p] = {"mkeys_s": n / med / 1e3, "ms": med, "sorted": ok,
+                      "frac_whole_sort_of_measured": pm * 2 * n * 4 / (med * 1e-3) / 1e9 / hbm}
+            del src, out
+        _line(args, dist, res["random"]["mkeys_s"], {"workload": f"{n} int32, seven patterns, seed 1", "n": n},
+              {"patterns": res}, ms=res["random"]["ms"])
+    elif w in ("records", "floats"):
+        n = 1 << 26
+        if w == "records":
+            r = records_u64(n, seed=1)
+            src = torch.from_numpy(r.view(np.int64)).cuda()
+            kind, es, dt = T.TSQS_U64_U64_REC, 16, "u64+u64 record"
+            desc = "2^26 records {u64 key, u64 payload}, 10% duplicated keys, 0.1% duplicated records"
+        else:
+            x = floats_normal_specials(n, seed=1)
+            src = torch.from_numpy(x).cuda()
+            kind, es, dt = T.TSQS_F32, 4, "float32 (totalOrder)"
+            desc = "2^26 float32 ~N(0,1) with 0.1% +-0, +-inf, NaNs (IEEE totalOrder)"
+        med, best, ok, out = _time_fresh(torch, T, src, kind, 5)
+        pm = p_min(n)
+        alg = pm * 2 * n * es
+        _line(args, dist, n / med / 1e3, {"workload": desc, "n": n, "dtype": dt},
+              {"sorted_status_ok": ok, "roofline_whole_sort": {
+                  "p_min": pm, "alg_bytes": alg, "achieved_gbs": alg / (med * 1e-3) / 1e9,
+                  "frac_of_measured": alg / (med * 1e-3) / 1e9 / hbm,
+                  "roofline_mkeys": hbm * 1e9 / (2 * pm * es) / 1e6}}, ms=med)
+    elif w == "batched":
+        batched_workload(args, dist, torch, T)
+    elif w == "serving":
+        serving_workload(args, dist, torch, T)
+
+
+def batched_workload(args, dist, torch, T):
+    """20,000 int32 segments, sizes floor(2^(20U)) in [1, 2^20], pattern per segment:
+    one graph-replayed segmented sort with an autotuned plan vs a loop of per-segment
+    tsqs_sort calls, on identical inputs, results compared byte for byte."""
+    from workloads.patterns import batched_segments, batched_keys
+    nseg = 20_000
+    offs, sizes, pat = batched_segments(nseg, seed=1)
+    x = batched_keys(offs, pat, seed=1)
+    total = int(offs[-1])
+    src = torch.from_numpy(x).cuda()
+    d_offs = torch.from_numpy(offs.astype(np.int64)).cuda()
+    del x
+    plan = T.Plan()
+    s = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    rc = T.lib().tsqs_plan_autotune(T.TSQS_I32, total, nseg, ctypes.c_void_p(s.cuda_stream),
+                                    ctypes.byref(plan))
+    tune_s = time.perf_counter() - t0
+    ctx = T.Context(plan) if rc == 0 else T.Context()
+    ctx.reserve(total, nseg, 4)
+    # batched: one segmented call per step
+    bt = []
+    for r in range(args.warmup + 3):
+        w = src.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        T.sort_segmented_(w, d_offs, kind=T.TSQS_I32, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= args.warmup:
+            bt.append(e0.elapsed_time(e1))
+    ok_b = ctx.status() == 0
+    out_b = w
+    # per call: one tsqs_sort per segment (same context, same plan)
+    w2 = src.clone()
+    lib = T.lib()
+    ptr = w2.data_ptr()
+    sp = ctypes.c_void_p(s.cuda_stream)
+    ofl = [int(o) for o in offs]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(nseg):
+        n = ofl[i + 1] - ofl[i]
+        if n > 1:
+            lib.tsqs_ctx_sort(ctx.handle, ctypes.c_void_p(ptr + 4 * ofl[i]), n, 4, T.TSQS_I32, sp)
+    e1.record()
+    torch.cuda.synchronize()
+    pc = e0.elapsed_time(e1)
+    same = bool(torch.equal(out_b, w2))
+    bmed = statistics.median(bt)
+    _line(args, dist, total / bmed / 1e3,
+          {"workload": "batched: 20,000 int32 segments, sizes floor(2^(20U)) in [1, 2^20], seven patterns",
+           "n_total": total, "nseg": nseg},
+          {"batched": {"ms": bmed, "mkeys_s": total / bmed / 1e3, "segs_s": nseg / bmed * 1e3,
+                       "status_ok": ok_b},
+           "per_call": {"ms": pc, "mkeys_s": total / pc / 1e3, "segs_s": nseg / pc * 1e3},
+           "batched_over_per_call": pc / bmed, "identical_results": same,
+           "plan": plan.as_dict(), "autotune_s": tune_s}, ms=bmed)
+
+
+def _gen_request(torch, kind_rec, n, pattern, seed, dev):
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    if kind_rec:
+        r = torch.randint(-2 ** 63, 2 ** 63 - 1, (n, 2), dtype=torch.int64, device=dev, generator=g)
+        h = max(1, n // 20)
+        dup = torch.randint(0, n, (2 * h,), device=dev, generator=g)
+        r[dup[:h], 0] = r[dup[h:], 0]
+        return r
+    i = torch.arange(n, device=dev, dtype=torch.int64)
+    if pattern == "random":
+        return torch.randint(-2 ** 31, 2 ** 31 - 1, (n,), dtype=torch.int32, device=dev, generator=g)
+    if pattern == "sorted":
+        return i.to(torch.int32)
+    if pattern == "reversed":
+        return (n - 1 - i).to(torch.int32)
+    if pattern == "organ_pipe":
+        return torch.where(i < n // 2, i + 1, n - i).to(torch.int32)
+    if pattern == "many_equals":
+        return torch.randint(0, 16, (n,), dtype=torch.int32, device=dev, generator=g)
+    if pattern == "stair_steps":
+        return (i // 1024).to(torch.int32)
+    a = i.to(torch.int32)
+    k = max(1, n // 200)
+    p1 = torch.randint(0, n, (k,), device=dev, generator=g)
+    p2 = torch.randint(0, n, (k,), device=dev, generator=g)
+    a[p1], a[p2] = a[p2].clone(), a[p1].clone()
+    return a
+
+
+def serving_workload(args, dist, torch, T):
+    """Poisson stream of sort requests, sizes floor(2^(10 + 14U)), 70% int32 / 30%
+    (u64, u64) records, patterns from the seven, admitted under a 40 GB budget.
+    The offered load is 0.7 x the sustained throughput measured with every request
+    submitted at once."""
+    from workloads import PATTERNS
+    from workloads.patterns import serving_requests
+    nreq = int(os.environ.get("TSQS_SERVE_REQUESTS", "2000"))
+    req = serving_requests(nreq, seed=1)
+    dev = torch.device("cuda")
+    bufs, pristine = [], []
+    for i in range(nreq):
+        t = _gen_request(torch, bool(req["is_rec"][i]), int(req["sizes"][i]),
+                         PATTERNS[int(req["pattern"][i])], i, dev)
+        pristine.append(t)
+    torch.cuda.synchronize()
+    keys = [int(x) for x in req["sizes"]]
+    total_keys = sum(keys)
+    lib = T.lib()
+
+    def run(lam):
+        work = [p.clone() for p in pristine]
+        torch.cuda.synchronize()
+        srv = lib.tsqs_server_create(40 << 30, 4, 256)
+        assert srv
+        arrive = np.cumsum(req["gaps"] / lam) if lam else np.zeros(nreq)
+        tickets = [None] * nreq
+        t0 = time.perf_counter()
+        i = 0
+        while True:
+            now = time.perf_counter() - t0
+            while i < nreq and arrive[i] <= now:
+                tk = ctypes.c_uint64()
+                kind, es = (T.TSQS_U64_U64_REC, 16) if req["is_rec"][i] else (T.TSQS_I32, 4)
+                rc = lib.tsqs_server_submit(srv, ctypes.c_void_p(work[i].data_ptr()), keys[i], es,
+                                            kind, ctypes.byref(tk))
+                assert rc == 0, rc
+                tickets[i] = tk.value
+                i += 1
+            left = lib.tsqs_server_progress(srv)
+            if i == nreq and left == 0:
+                break
+        res = []
+        for k in range(nreq):
+            r = T.Result()
+            lib.tsqs_server_poll(srv, tickets[k], ctypes.byref(r))
+            res.append((r.t_submit, r.t_start, r.t_done, r.status, r.batch_size, r.batch_id))
+        lib.tsqs_server_destroy(srv)
+        t_sub = np.array([x[0] for x in res])
+        t_done = np.array([x[2] for x in res])
+        lat = (t_done - t_sub) * 1e3
+        span = t_done.max() - t_sub.min()
+        ok = all(x[3] == 0 for x in res)
+        sorted_ok = all(bool((w[1:] >= w[:-1]).all().item()) if w.dim() == 1 else True for w in work[:50])
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "sustained_mkeys_s": total_keys / span / 1e6,
+                "span_s": span, "status_ok": ok, "spot_sorted": sorted_ok,
+                "batches": len(set(x[5] for x in res)),
+                "mean_batch": float(np.mean([x[4] for x in res]))}
+
+    run(None)                                             # warm graphs and lanes
+    sat = run(None)
+    lam = 0.7 * sat["sustained_mkeys_s"] * 1e6 / (total_keys / nreq)
+    load = run(lam)
+    _line(args, dist, load["sustained_mkeys_s"],
+          {"workload": f"serving: {nreq} Poisson requests, sizes 2^10..2^24 log-uniform, 70% int32 / "
+                       "30% u64+u64 records, seven patterns, 40 GB budget, 4 lanes",
+           "requests": nreq, "offered_load_req_s": lam},
+          {"at_offered_load": load, "saturated": sat}, ms=load["mean_ms"])
 
 
 def main():

@@ -201,6 +201,9 @@ void tsqs_debug_withhold_publish(int on);
  * ------------------------------------------------------------------------------- */
 int tsqs_plan_autotune(int key_kind, size_t n_hint, size_t nseg_hint, void *stream,
                        tsqs_plan *out);
+/* Writes / reads the autotuned plans of this process as text (one plan per line). */
+int tsqs_plan_cache_save(const char *path);
+int tsqs_plan_cache_load(const char *path);
 
 /* ---------------------------------------------------------------------------------
  * Serving: continuous batching of sort requests that arrive over time.

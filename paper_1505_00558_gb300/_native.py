@@ -80,6 +80,8 @@ SIGNATURES = {
     "tsqs_debug_set_spin_limit": (None, [_u32]),
     "tsqs_debug_withhold_publish": (None, [_i]),
     "tsqs_plan_autotune": (_i, [_i, _sz, _sz, _vp, ctypes.POINTER(Plan)]),
+    "tsqs_plan_cache_save": (_i, [ctypes.c_char_p]),
+    "tsqs_plan_cache_load": (_i, [ctypes.c_char_p]),
     "tsqs_server_create": (_vp, [_sz, _i, _i]),
     "tsqs_server_submit": (_i, [_vp, _vp, _sz, _sz, _i, _pu64]),
     "tsqs_server_progress": (_i, [_vp]),

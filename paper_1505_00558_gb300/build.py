@@ -14,8 +14,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsqs.so")
 
-SOURCES = ["tsqs_common.cu", "tsqs_k4.cu", "tsqs_k8.cu", "tsqs_k16.cu", "tsqs_host.cu"]
-EXTRA = ["tsqs_server.cpp", "tsqs_autotune.cpp"]
+SOURCES = ["tsqs_common.cu", "tsqs_k4.cu", "tsqs_k8.cu", "tsqs_k16.cu", "tsqs_host.cu",
+           "tsqs_autotune.cu", "tsqs_server.cu"]
+EXTRA: list[str] = []
 
 
 def _cuda_home() -> str:

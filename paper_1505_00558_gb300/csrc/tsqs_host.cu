@@ -25,6 +25,7 @@ using namespace tsqs;
 namespace tsqs {
 __global__ void k_setup(Job *job, Ctl *ctl, Job j);
 }
+bool tsqs_cached_plan(int kind, size_t n, size_t nseg, tsqs_plan *out);
 
 namespace {
 
@@ -492,6 +493,10 @@ int tsqs_ctx_stats(tsqs_ctx *c, void *stream, tsqs_stats *out) {
 
 int tsqs_plan_default(int key_kind, size_t n_hint, tsqs_plan *out) {
     if (!out || !get_ops(key_kind)) return TSQS_EINVAL;
+    if (n_hint && tsqs_cached_plan(key_kind, n_hint, 1, out)) {
+        normalise_plan(out);
+        return TSQS_OK;
+    }
     fill_default_plan(key_kind, n_hint, out);
     normalise_plan(out);
     return TSQS_OK;
