@@ -63,7 +63,9 @@ typedef enum {
 typedef struct {
     int32_t  tile_items;       /* partition kernel shape, 0..3 (0 = default): consumer
                                   threads x keys per thread x ring depth; see the design doc */
-    int32_t  small_threshold;  /* segments of <= this many elements finish on chip (<= 4096) */
+    int32_t  small_threshold;  /* segments of <= this many elements finish on chip, 512..4096;
+                                  capped per kind at 4096 (4-byte), 2048 (8-byte), 1024
+                                  (records): the largest leaf one warp holds in registers */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
     int32_t  sample_count;     /* pivot sample size: 15, 31 or 63                      */
     int32_t  offset_mode;      /* where a tile writes its <p and >p runs:

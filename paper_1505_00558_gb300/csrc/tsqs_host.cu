@@ -63,9 +63,14 @@ struct Layout {
 //   tiles     <= n/TILE + 2 per segment (partial first and last tiles)
 //   leaves    <= 2 children per partitioned segment, n/kFillChunk + 1 fill items per
 //             segment, plus the small root segments
-Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int tile) {
+// Effective on-chip threshold: the plan's, capped by what the kind's leaf kernel holds.
+size_t eff_threshold(const tsqs_plan &plan, int leaf_max) {
+    return std::min<size_t>((size_t)plan.small_threshold, (size_t)leaf_max);
+}
+
+Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int tile, int leaf_max) {
     Layout L{};
-    const size_t T = (size_t)plan.small_threshold;
+    const size_t T = eff_threshold(plan, leaf_max);
     const size_t cf = n / (T + 1) + nseg + 4;
     const size_t ct = n / (size_t)tile + 2 * cf + 4;
     const size_t cl = 3 * cf + n / kFillChunk + nseg + 4;
@@ -103,7 +108,7 @@ void normalise_plan(tsqs_plan *p) {
     fill_default_plan(TSQS_I32, 0, &d);
     if (p->small_threshold <= 0) p->small_threshold = d.small_threshold;
     if (p->small_threshold > kMaxSmall) p->small_threshold = kMaxSmall;
-    if (p->small_threshold < 64) p->small_threshold = 64;
+    if (p->small_threshold < 512) p->small_threshold = 512;
     if (p->sample_count <= 0) p->sample_count = d.sample_count;
     if (p->sample_count > kMaxSamples) p->sample_count = kMaxSamples;
     if ((p->sample_count & 1) == 0) p->sample_count -= 1;
@@ -186,8 +191,8 @@ int ctx_quiesce(tsqs_ctx *c) {
     return TSQS_OK;
 }
 
-int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile) {
-    const Layout L = make_layout(n, nseg, es, c->plan, tile);
+int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile, int leaf_max) {
+    const Layout L = make_layout(n, nseg, es, c->plan, tile, leaf_max);
     if (c->scratch && L.total <= c->scratch_bytes) return TSQS_OK;
     int rc = ctx_quiesce(c);
     if (rc) return rc;
@@ -212,7 +217,7 @@ int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile) 
 int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t *offs,
              size_t nseg, Job *j) {
     const size_t es = (size_t)o->elem_size;
-    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile);
+    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile, o->leaf_max);
     if (L.total > c->scratch_bytes) return TSQS_EINTERNAL;
     memset(j, 0, sizeof(*j));
     const uintptr_t b = (uintptr_t)base;
@@ -232,7 +237,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
-    j->small_T = (uint32_t)c->plan.small_threshold;
+    j->small_T = (uint32_t)eff_threshold(c->plan, o->leaf_max);
     j->samples = (uint32_t)c->plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));
     j->spin_limit = g_debug_spin ? g_debug_spin : kDefaultSpin;
@@ -336,7 +341,7 @@ int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t n
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, part_of(o, c->plan).tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
     if ((rc = ctx_build_graph(c, o))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, n, offs, nseg, &j))) return rc;
@@ -449,7 +454,8 @@ int tsqs_ctx_reserve(tsqs_ctx *c, size_t nmemb_total, size_t nseg, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     int rc = ctx_init_device(c);
     if (rc) return rc;
-    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, part_of(o, c->plan).tile);
+    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, part_of(o, c->plan).tile,
+                              o->leaf_max);
 }
 
 size_t tsqs_ctx_scratch_bytes(const tsqs_ctx *c) { return c ? c->scratch_bytes : 0; }
@@ -462,7 +468,7 @@ size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
     tsqs_plan p;
     if (plan) p = *plan; else fill_default_plan(kind, nmemb_total, &p);
     normalise_plan(&p);
-    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, part_of(o, p).tile).total;
+    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, part_of(o, p).tile, o->leaf_max).total;
 }
 
 int tsqs_ctx_device_status(tsqs_ctx *c, void *stream) {
@@ -579,7 +585,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, nmemb, nullptr, 0, &j))) return rc;
     if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
@@ -649,10 +655,10 @@ int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_k
     const KindOps *o = get_ops(key_kind);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)base, nmemb, nullptr, 0, &j))) return rc;
-    const Layout L = make_layout(nmemb, 1, elem_size, c->plan, part_of(o, c->plan).tile);
+    const Layout L = make_layout(nmemb, 1, elem_size, c->plan, part_of(o, c->plan).tile, o->leaf_max);
     char *misc = c->scratch + L.misc_off;
     uint64_t *d_offs = (uint64_t *)misc;
     uint64_t *d_pos = (uint64_t *)(misc + 64);
@@ -696,7 +702,7 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, part_of(o, c->plan).tile))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)src, nmemb, d_seg_offsets, nseg, &j))) return rc;
     j.alt = dst;

@@ -106,6 +106,7 @@ struct KindOps {
     int elem_size;
     int leaf_block, pivot_block;
     int leaf_smem;            // dynamic shared memory of the leaf kernel
+    int leaf_max;             // largest segment the leaf kernel sorts (32 x keys per lane)
     PartVariant part[kPartVariants];   // [0] is the default shape
     const void *k_init, *k_leaf, *k_pivot, *k_finish;
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;

@@ -4,7 +4,7 @@
 namespace tsqs {
 
 namespace {
-constexpr int kLeafBlock = 256, kPivotBlock = 256;
+constexpr int kLeafBlock = 512, kLeafMaxE = 8, kPivotBlock = 256;
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
 PartVariant part_variant() {
@@ -25,12 +25,13 @@ KindOps make_ops() {
     o.leaf_block = kLeafBlock;
     o.pivot_block = kPivotBlock;
     o.leaf_smem = (kMaxSmall + kMaxSmall / 32) * (int)sizeof(typename Key<KIND>::C);
+    o.leaf_max = kMaxSmall;
     o.part[0] = part_variant<KIND, 256, 4, 3>();
     o.part[1] = part_variant<KIND, 256, 4, 4>();
     o.part[2] = part_variant<KIND, 512, 4, 2>();
     o.part[3] = part_variant<KIND, 128, 4, 4>();
     o.k_init = (const void *)k_init<KIND>;
-    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, 1>;
+    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 1>;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;

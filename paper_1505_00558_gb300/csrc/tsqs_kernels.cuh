@@ -771,12 +771,15 @@ __global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 
 
 // ---------------------------------------------------------------------------------
 // Leaf pass (persistent): on-chip sort of small segments and =p fills.
-// A segment of len <= 4096 is padded with the largest canonical key to
-// P = max(32, 2^ceil(log2 len)) and sorted by a bitonic network held in registers:
-// thread t owns elements [t E, t E + E) (E = 16 for P >= 512, else P / 32 in one
-// warp).  Compare-exchanges between elements of one thread run on registers,
-// between lanes of a warp through shuffles, and only strides of 32 E or more go
-// through shared memory.
+// One block (LB threads) per leaf item.  A segment of len <= 4096 elements is padded
+// with the largest canonical key to P = max(32, 2^ceil(log2 len)); thread t owns the
+// E consecutive elements [t E, t E + E), E = min(32, P / 32), so P / E threads work.
+// The network is the bitonic sort in its "mirror" form: each merge of width k first
+// compares element i with i ^ (k - 1), then runs half-cleaners i vs i ^ j
+// (j = k/4 .. 1), and every comparator puts the minimum at the lower index, so all
+// in-thread comparators have compile-time directions.  Strides below E stay inside a
+// thread, strides below 32 E cross lanes through __shfl_xor_sync, larger strides go
+// through shared memory (one pad word per 32 keeps the accesses conflict-free).
 // ---------------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned int c_min(unsigned int a, unsigned int b) { return min(a, b); }
@@ -791,45 +794,60 @@ __device__ __forceinline__ U128 c_shfl_xor(U128 v, int m) {
     return U128{__shfl_xor_sync(0xffffffffu, v.lo, m), __shfl_xor_sync(0xffffffffu, v.hi, m)};
 }
 
+// min to the lower index, max to the upper
 template <class C>
-__device__ __forceinline__ void cmpx(C &a, C &b, bool asc) {
-    const C lo = c_min(a, b), hi = c_maxv(a, b);
-    a = asc ? lo : hi;
-    b = asc ? hi : lo;
+__device__ __forceinline__ void cx(C &lo, C &hi) {
+    const C a = lo, b = hi;
+    lo = c_min(a, b);
+    hi = c_maxv(a, b);
 }
 
-// Sorts s[0, P) ascending (P a power of two, 32 E <= P <= E * blockDim.x).  Every
-// thread of the block must call it (it contains block barriers).
-// Shared-memory index with one pad word per 32: the blocked layout (stride E) and the
-// cross-warp partners then fall into distinct banks.
 __device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
 
+// Sorts s[0, P) ascending; P a power of two with 32 E <= P <= E * blockDim.x.  Every
+// thread of the block must call it (it contains block barriers).
 template <class C, int E>
-__device__ __forceinline__ void bitonic_regs(C *s, uint32_t P) {
-    const uint32_t t = threadIdx.x;
+__device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P) {
+    const uint32_t t = threadIdx.x, lane = t & 31u;
     const uint32_t NT = P / E;
     const bool act = t < NT;
     C v[E];
     if (act) {
 #pragma unroll
         for (int r = 0; r < E; r++) v[r] = s[pad32(t * E + r)];
-        // merges of width k <= E: all inside the thread
+        // merges of width k <= E: inside the thread
 #pragma unroll
         for (int k = 2; k <= E; k <<= 1) {
 #pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int r = 0; r < E; r++) {
+                const int q = r ^ (k - 1);
+                if (q > r) cx(v[r], v[q]);
+            }
 #pragma unroll
-                for (int r = 0; r < E; r++) {
-                    const int q = r ^ j;
-                    if (q > r) cmpx(v[r], v[q], ((t * E + r) & (uint32_t)k) == 0u);
-                }
+            for (int j = k >> 2; j >= 1; j >>= 1) {
+#pragma unroll
+                for (int r = 0; r < E; r++)
+                    if ((r & j) == 0) cx(v[r], v[r | j]);
             }
         }
     }
     for (uint32_t k = 2 * E; k <= P; k <<= 1) {
-        const bool asc = ((t * E) & k) == 0u;
-        // strides across warps: through shared memory
-        for (uint32_t j = k >> 1; j >= 32u * E; j >>= 1) {
+        // ---- mirror stage: element i vs i ^ (k - 1)
+        if (k <= 32u * E) {
+            if (act) {                                   // partner lane t ^ (k/E - 1), register E-1-r
+                const int lm = (int)(k / E - 1);
+                const bool lower = (t & (k / (2 * E))) == 0u;
+#pragma unroll
+                for (int r = 0; r < (E + 1) / 2; r++) {
+                    const C wa = c_shfl_xor(v[E - 1 - r], lm);
+                    if (r != E - 1 - r) {
+                        const C wb = c_shfl_xor(v[r], lm);
+                        v[E - 1 - r] = lower ? c_min(v[E - 1 - r], wb) : c_maxv(v[E - 1 - r], wb);
+                    }
+                    v[r] = lower ? c_min(v[r], wa) : c_maxv(v[r], wa);
+                }
+            }
+        } else {                                         // across warps: shared memory
             __syncthreads();
             if (act) {
 #pragma unroll
@@ -837,34 +855,48 @@ __device__ __forceinline__ void bitonic_regs(C *s, uint32_t P) {
             }
             __syncthreads();
             if (act) {
-                const bool keep_min = (((t * E) & j) == 0u) == asc;
+                const bool lower = ((t * E) & (k >> 1)) == 0u;
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const C w = s[pad32((t * E + r) ^ (k - 1))];
+                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
+                }
+            }
+        }
+        // ---- half-cleaners across warps
+        for (uint32_t j = k >> 2; j >= 32u * E; j >>= 1) {
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+            }
+            __syncthreads();
+            if (act) {
+                const bool lower = ((t * E) & j) == 0u;
 #pragma unroll
                 for (int r = 0; r < E; r++) {
                     const C w = s[pad32((t * E + r) ^ j)];
-                    v[r] = keep_min ? c_min(v[r], w) : c_maxv(v[r], w);
+                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
                 }
             }
         }
         if (act) {
-            // strides across lanes: shuffles
-            const uint32_t jtop = min(k >> 1, 16u * E);
-            for (uint32_t j = jtop; j >= (uint32_t)E; j >>= 1) {
+            // ---- half-cleaners across lanes
+            for (uint32_t j = min(k >> 2, 16u * E); j >= (uint32_t)E; j >>= 1) {
                 const int lm = (int)(j / E);
-                const bool keep_min = ((t & (uint32_t)lm) == 0u) == asc;
+                const bool lower = (lane & (uint32_t)lm) == 0u;
 #pragma unroll
                 for (int r = 0; r < E; r++) {
                     const C w = c_shfl_xor(v[r], lm);
-                    v[r] = keep_min ? c_min(v[r], w) : c_maxv(v[r], w);
+                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
                 }
             }
-            // strides inside the thread
+            // ---- half-cleaners inside the thread
 #pragma unroll
-            for (int j = E >> 1; j > 0; j >>= 1) {
+            for (int j = E >> 1; j >= 1; j >>= 1) {
 #pragma unroll
-                for (int r = 0; r < E; r++) {
-                    const int q = r ^ j;
-                    if (q > r) cmpx(v[r], v[q], asc);
-                }
+                for (int r = 0; r < E; r++)
+                    if ((r & j) == 0) cx(v[r], v[r | j]);
             }
         }
     }
@@ -876,12 +908,12 @@ __device__ __forceinline__ void bitonic_regs(C *s, uint32_t P) {
     __syncthreads();
 }
 
-template <int KIND, int LB, int MINB>
+template <int KIND, int LB, int MAXE, int MINB>
 __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
-    static_assert(LB * 16 >= kMaxSmall, "block too small for the largest leaf");
+    static_assert(LB * MAXE >= kMaxSmall, "block too small for the largest leaf");
     extern __shared__ __align__(16) unsigned char leaf_raw[];
     C *s = reinterpret_cast<C *>(leaf_raw);
     __shared__ uint32_t s_item;
@@ -900,7 +932,16 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         items++;
         if (it.kind == LEAF_FILL) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
-            for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = val;
+            S rep[K::V];
+#pragma unroll
+            for (int j = 0; j < K::V; j++) rep[j] = val;
+            const uint64_t x = it.begin;
+            uint32_t head = (uint32_t)((K::V - ((x + job->vec_off) % K::V)) % K::V);
+            if (head > it.len) head = it.len;
+            const uint32_t nvec = (it.len - head) / K::V, body_end = head + nvec * K::V;
+            if (threadIdx.x < head) out[x + threadIdx.x] = val;
+            for (uint32_t q = threadIdx.x; q < nvec; q += LB) stg_vec<S, K::V>(out + x + head + q * K::V, rep);
+            for (uint32_t i = body_end + threadIdx.x; i < it.len; i += LB) out[x + i] = val;
             filled += it.len;
         } else if (it.len > (uint32_t)kMaxSmall) {
             if (threadIdx.x == 0) set_status(ctl, TSQS_EINTERNAL);
@@ -911,12 +952,14 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             for (uint32_t i = threadIdx.x; i < P; i += LB)
                 s[pad32(i)] = i < len ? K::canon(src[it.begin + i]) : c_max<C>();
             __syncthreads();
-            // keep every thread busy: E = P / LB elements each once P >= 32 * LB / 8
-            if (P >= 16u * LB) bitonic_regs<C, 16>(s, P);
-            else if (P >= 8u * LB) bitonic_regs<C, 8>(s, P);
-            else if (P >= 4u * LB) bitonic_regs<C, 4>(s, P);
-            else if (P >= 2u * LB) bitonic_regs<C, 2>(s, P);
-            else bitonic_regs<C, 1>(s, P);
+            // E = min(MAXE, P / 32) keys per thread
+            const uint32_t E = min((uint32_t)MAXE, P / 32u);
+            if (E == 1) bitonic_mirror<C, 1>(s, P);
+            else if (E == 2) bitonic_mirror<C, 2>(s, P);
+            else if (E == 4) bitonic_mirror<C, 4>(s, P);
+            else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P);
+            else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P);
+            else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P);
             for (uint32_t i = threadIdx.x; i < len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
             sorted += len;
         }
