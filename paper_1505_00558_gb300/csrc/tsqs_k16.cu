@@ -24,7 +24,7 @@ KindOps make_ops() {
     o.elem_size = 16;
     o.leaf_block = kLeafBlock;
     o.pivot_block = kPivotBlock;
-    o.leaf_smem = (kMaxSmall + kMaxSmall / 32) * (int)sizeof(typename Key<KIND>::C);
+    o.leaf_smem = (int)LeafLayout<KIND>::bytes;
     o.leaf_max = kMaxSmall;
     o.part[0] = part_variant<KIND, 256, 4, 3>();
     o.part[1] = part_variant<KIND, 256, 4, 4>();

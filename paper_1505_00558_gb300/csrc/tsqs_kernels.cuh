@@ -363,7 +363,8 @@ __device__ typename K::C sample_pivot(const typename K::S *src, uint64_t b, uint
     return piv;
 }
 
-// One block per frontier segment (grid-stride): pivot by warp 0, tile tables by all.
+// One warp per frontier segment (grid-stride over warps): the sampled median, then the
+// segment's rows of the tile table.
 template <int KIND>
 __global__ void k_pivot(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
@@ -371,20 +372,23 @@ __global__ void k_pivot(const Job *__restrict__ job, Ctl *ctl) {
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
     const uint32_t nf = min(ctl->nfront[par], job->cap_front);
     const typename K::S *src = buffer<K>(job, par);
-    for (uint32_t si = blockIdx.x; si < nf; si += gridDim.x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    const bool lb = job->offset_mode != 0u;
+    for (uint32_t si = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); si < nf; si += warps) {
         SegDesc *d = &job->front[par][si];
         const uint64_t b = d->begin, e = d->end;
         const uint32_t tb = d->tile_begin, nt = d->ntiles;
-        if (threadIdx.x < 32) {
-            const typename K::C p = sample_pivot<K>(src, b, e, job->samples, job->seed, nullptr);
-            if (threadIdx.x == 0) c_words(p, d->piv_lo, d->piv_hi);
+        const typename K::C p = sample_pivot<K>(src, b, e, job->samples, job->seed, nullptr);
+        if (lane == 0) {
+            c_words(p, d->piv_lo, d->piv_hi);
+            job->seg_done[si] = 0u;
+            job->seg_cursor[si] = 0ull;
         }
-        const bool lb = job->offset_mode != 0u;
-        for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+        for (uint32_t t = lane; t < nt; t += 32u) {
             job->tile_seg[tb + t] = si;
             if (lb) job->tile_status[tb + t] = 0ull;
         }
-        if (threadIdx.x == 0) { job->seg_done[si] = 0u; job->seg_cursor[si] = 0ull; }
     }
 }
 
@@ -908,50 +912,122 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P) {
     __syncthreads();
 }
 
+// Shared-memory layout of the leaf kernel: the padded sort buffer, then two raw
+// prefetch slots (a leaf's 16-byte-aligned hull) and their mbarriers.
+template <int KIND>
+struct LeafLayout {
+    using S = typename Key<KIND>::S;
+    using C = typename Key<KIND>::C;
+    static constexpr int PRE = kMaxSmall + 2 * Key<KIND>::V;          // elements per slot
+    static constexpr size_t sort_bytes = ((kMaxSmall + kMaxSmall / 32) * sizeof(C) + 127) / 128 * 128;
+    static constexpr size_t off_pre = sort_bytes;
+    static constexpr size_t off_bar = off_pre + 2 * (size_t)PRE * sizeof(S);
+    static constexpr size_t bytes = off_bar + 2 * sizeof(unsigned long long);
+};
+
 template <int KIND, int LB, int MAXE, int MINB>
 __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
+    using LY = LeafLayout<KIND>;
+    constexpr int V = K::V;
     static_assert(LB * MAXE >= kMaxSmall, "block too small for the largest leaf");
-    extern __shared__ __align__(16) unsigned char leaf_raw[];
+    extern __shared__ __align__(128) unsigned char leaf_raw[];
     C *s = reinterpret_cast<C *>(leaf_raw);
-    __shared__ uint32_t s_item;
+    S *pre = reinterpret_cast<S *>(leaf_raw + LY::off_pre);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(leaf_raw + LY::off_bar);
+    __shared__ LeafItem s_it[2];
+    __shared__ int64_t s_cs[2], s_ce[2];
+    __shared__ uint32_t s_ok[2];
     const int par = ctl->level & 1;
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
     const uint32_t nl = min(ctl->nleaf[par], job->cap_leaves);
     const S *src = buffer<K>(job, par);          // may be the same buffer as out
     S *out = reinterpret_cast<S *>(job->base);
-    uint64_t sorted = 0, filled = 0, items = 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->leaf_claim, 1u);
-        __syncthreads();
-        const uint32_t ii = s_item;
-        if (ii >= nl) break;
+    const int64_t n = (int64_t)job->n;
+    const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
+    const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
+    const uint32_t wait_limit = 1u << 20;
+
+    // thread 0: claim the next item into `slot` and start the bulk copy of its hull
+    auto claim = [&](int slot) {
+        const uint32_t ii = atomicAdd(&ctl->leaf_claim, 1u);
+        if (ii >= nl) { s_ok[slot] = 0u; return; }
         const LeafItem it = job->leaves[par][ii];
+        s_it[slot] = it;
+        s_ok[slot] = 1u;
+        s_cs[slot] = s_ce[slot] = 0;
+        if (it.kind == LEAF_SORT && it.len <= (uint32_t)kMaxSmall) {
+            const int64_t b = (int64_t)it.begin, e = b + it.len;
+            const int64_t cs = max(b - ((b + (int64_t)job->vec_off) % V), e_lo);
+            const int64_t ce = min(e + ((V - ((e + (int64_t)job->vec_off) % V)) % V), e_hi);
+            if (ce > cs) {
+                s_cs[slot] = cs;
+                s_ce[slot] = ce;
+                const uint32_t bytes = (uint32_t)((ce - cs) * (int64_t)sizeof(S));
+                mbar_arrive_tx(&bar[slot], bytes);
+                tma_load_1d(pre + (size_t)slot * LY::PRE, src + cs, bytes, &bar[slot]);
+            }
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        claim(0);
+    }
+    __syncthreads();
+    uint32_t phase[2] = {0u, 0u};
+    uint64_t sorted = 0, filled = 0, items = 0;
+    for (uint32_t iter = 0;; iter++) {
+        const int sl = (int)(iter & 1u);
+        if (!s_ok[sl]) break;
+        const LeafItem it = s_it[sl];
+        const int64_t cs = s_cs[sl], ce = s_ce[sl];
         items++;
+        const bool is_sort = it.kind != LEAF_FILL && it.len <= (uint32_t)kMaxSmall;
+        uint32_t P = 32;
+        if (is_sort) {
+            if (ce > cs) {
+                if (!mbar_wait(&bar[sl], phase[sl], wait_limit)) {
+                    if (threadIdx.x == 0) set_status(ctl, TSQS_ETIMEOUT);
+                    mbar_wait(&bar[sl], phase[sl], wait_limit);   // let the copy land
+                }
+                phase[sl] ^= 1u;
+            }
+            const S *slot = pre + (size_t)sl * LY::PRE;
+            while (P < it.len) P <<= 1;
+#pragma unroll 4
+            for (uint32_t i = threadIdx.x; i < P; i += LB) {
+                C c = c_max<C>();
+                if (i < it.len) {
+                    const int64_t e = (int64_t)it.begin + i;
+                    c = K::canon((e >= cs && e < ce) ? slot[e - cs] : src[e]);
+                }
+                s[pad32(i)] = c;
+            }
+        }
+        fence_proxy_async();                // this slot's reads precede its next bulk copy
+        __syncthreads();                    // sort buffer loaded, slot free, s_it read
+        if (threadIdx.x == 0) claim(sl ^ 1);            // prefetch the next item meanwhile
         if (it.kind == LEAF_FILL) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
-            S rep[K::V];
+            S rep[V];
 #pragma unroll
-            for (int j = 0; j < K::V; j++) rep[j] = val;
+            for (int j = 0; j < V; j++) rep[j] = val;
             const uint64_t x = it.begin;
-            uint32_t head = (uint32_t)((K::V - ((x + job->vec_off) % K::V)) % K::V);
+            uint32_t head = (uint32_t)((V - ((x + job->vec_off) % V)) % V);
             if (head > it.len) head = it.len;
-            const uint32_t nvec = (it.len - head) / K::V, body_end = head + nvec * K::V;
+            const uint32_t nvec = (it.len - head) / V, body_end = head + nvec * V;
             if (threadIdx.x < head) out[x + threadIdx.x] = val;
-            for (uint32_t q = threadIdx.x; q < nvec; q += LB) stg_vec<S, K::V>(out + x + head + q * K::V, rep);
+            for (uint32_t q = threadIdx.x; q < nvec; q += LB) stg_vec<S, V>(out + x + head + q * V, rep);
             for (uint32_t i = body_end + threadIdx.x; i < it.len; i += LB) out[x + i] = val;
             filled += it.len;
-        } else if (it.len > (uint32_t)kMaxSmall) {
+        } else if (!is_sort) {
             if (threadIdx.x == 0) set_status(ctl, TSQS_EINTERNAL);
         } else {
-            const uint32_t len = it.len;
-            uint32_t P = 32;
-            while (P < len) P <<= 1;
-            for (uint32_t i = threadIdx.x; i < P; i += LB)
-                s[pad32(i)] = i < len ? K::canon(src[it.begin + i]) : c_max<C>();
-            __syncthreads();
             // E = min(MAXE, P / 32) keys per thread
             const uint32_t E = min((uint32_t)MAXE, P / 32u);
             if (E == 1) bitonic_mirror<C, 1>(s, P);
@@ -960,10 +1036,10 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P);
             else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P);
             else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P);
-            for (uint32_t i = threadIdx.x; i < len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
-            sorted += len;
+            for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
+            sorted += it.len;
         }
-        __syncthreads();
+        __syncthreads();                    // sort buffer free, next item's meta visible
     }
     if (threadIdx.x == 0 && items) {
         atomicAdd((unsigned long long *)&ctl->leaf_sorted, (unsigned long long)sorted);
@@ -1055,34 +1131,113 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
     const bool ok_state = *(volatile uint32_t *)&ctl->status == 0u;
     const uint32_t nf = min(ctl->nfront[par], job->cap_front);
     const int np = par ^ 1;
-    for (uint32_t si = blockIdx.x * blockDim.x + threadIdx.x; ok_state && si < nf;
-         si += gridDim.x * blockDim.x) {
-        const SegDesc sd = job->front[par][si];
-        uint64_t nlt, ngt;
-        const bool ok = seg_totals(job, si, sd.tile_begin, sd.ntiles, nlt, ngt);
-        const uint64_t m = sd.end - sd.begin;
-        if (!ok || nlt + ngt >= m) {
-            // p is an element of the segment, so the =p run is never empty; a violation
-            // means corrupted state: stop instead of looping forever
-            set_status(ctl, TSQS_EINTERNAL);
-            continue;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t T = job->small_T;
+    const int TILE = (int)job->tile;
+    // every lane takes one segment; a warp makes one atomic per counter for all its
+    // pushes (frontier entries, tiles, leaf items, keys) and hands out the offsets
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t base0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint32_t wb = base0; ok_state && wb < nf; wb += stride) {
+        const uint32_t si = wb + lane;
+        const bool have = si < nf;
+        uint64_t cb[2] = {0, 0}, ce[2] = {0, 0}, eqb = 0, eqe = 0;
+        uint64_t piv_lo = 0, piv_hi = 0;
+        bool bad = false;
+        if (have) {
+            const SegDesc sd = job->front[par][si];
+            uint64_t nlt, ngt;
+            const bool ok = seg_totals(job, si, sd.tile_begin, sd.ntiles, nlt, ngt);
+            const uint64_t m = sd.end - sd.begin;
+            if (!ok || nlt + ngt >= m) {
+                // p is an element of the segment, so the =p run is never empty; a
+                // violation means corrupted state: stop instead of looping forever
+                bad = true;
+            } else {
+                cb[0] = sd.begin; ce[0] = sd.begin + nlt;
+                cb[1] = sd.end - ngt; ce[1] = sd.end;
+                eqb = sd.begin + nlt; eqe = sd.end - ngt;
+                piv_lo = sd.piv_lo; piv_hi = sd.piv_hi;
+            }
         }
-        push_segment<K::V>(job, ctl, np, sd.begin, sd.begin + nlt);
-        push_segment<K::V>(job, ctl, np, sd.end - ngt, sd.end);
-        const uint64_t eqb = sd.begin + nlt, eqe = sd.end - ngt;
+        if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(ctl, TSQS_EINTERNAL);
+        // per lane: up to two frontier pushes, two leaf pushes, and nch fill items
+        uint32_t nfr = 0, ntl = 0, nlf = 0;
+        uint64_t keys = 0;
+        int64_t s0[2] = {0, 0};
+        uint32_t ntc[2] = {0, 0};
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const uint64_t msz = ce[c] - cb[c];
+            if (msz > T) {
+                s0[c] = tile_origin<K::V>(cb[c], job->vec_off);
+                ntc[c] = tiles_for(ce[c], s0[c], TILE);
+                nfr++; ntl += ntc[c]; keys += msz;
+            } else if (msz >= 1) {
+                nlf++;
+            }
+        }
         const uint32_t nch = (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
-        const uint32_t fb = atomicAdd(&ctl->nleaf[np], nch);
-        if ((uint64_t)fb + nch > job->cap_leaves) { set_status(ctl, TSQS_EINTERNAL); continue; }
+        nlf += nch;
+        // warp-exclusive offsets and one atomic per counter
+        uint32_t xf = nfr, xt = ntl, xl = nlf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xffffffffu, xf, o);
+            const uint32_t b2 = __shfl_up_sync(0xffffffffu, xt, o);
+            const uint32_t c2 = __shfl_up_sync(0xffffffffu, xl, o);
+            if (lane >= (uint32_t)o) { xf += a; xt += b2; xl += c2; }
+        }
+        uint64_t ksum = keys;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ksum += __shfl_xor_sync(0xffffffffu, ksum, o);
+        uint32_t bf = 0, bt = 0, bl = 0;
+        if (lane == 31) {
+            bf = atomicAdd(&ctl->nfront[np], xf);
+            bt = atomicAdd(&ctl->ntiles[np], xt);
+            bl = atomicAdd(&ctl->nleaf[np], xl);
+            if (ksum) atomicAdd((unsigned long long *)&ctl->front_keys[np], (unsigned long long)ksum);
+        }
+        bf = __shfl_sync(0xffffffffu, bf, 31) + xf - nfr;
+        bt = __shfl_sync(0xffffffffu, bt, 31) + xt - ntl;
+        bl = __shfl_sync(0xffffffffu, bl, 31) + xl - nlf;
+        // write this lane's pushes
+        bool overflow = false;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const uint64_t msz = ce[c] - cb[c];
+            if (msz > T) {
+                if (bf >= job->cap_front || (uint64_t)bt + ntc[c] > job->cap_tiles) {
+                    overflow = true;
+                } else {
+                    SegDesc d;
+                    d.begin = cb[c]; d.end = ce[c]; d.s0 = s0[c]; d.tile_begin = bt; d.ntiles = ntc[c];
+                    d.piv_lo = 0; d.piv_hi = 0;
+                    job->front[np][bf] = d;
+                }
+                bf++; bt += ntc[c];
+            } else if (msz >= 1) {
+                if (bl >= job->cap_leaves) overflow = true;
+                else {
+                    LeafItem it;
+                    it.begin = cb[c]; it.len = (uint32_t)msz; it.kind = LEAF_SORT; it.v_lo = 0; it.v_hi = 0;
+                    job->leaves[np][bl] = it;
+                }
+                bl++;
+            }
+        }
         for (uint32_t c = 0; c < nch; c++) {
+            if (bl + c >= job->cap_leaves) { overflow = true; break; }
             LeafItem li;
             li.begin = eqb + (uint64_t)c * kFillChunk;
             const uint64_t rest = eqe - li.begin;
             li.len = (uint32_t)(rest < kFillChunk ? rest : kFillChunk);
             li.kind = LEAF_FILL;
-            li.v_lo = sd.piv_lo;
-            li.v_hi = sd.piv_hi;
-            job->leaves[np][fb + c] = li;
+            li.v_lo = piv_lo;
+            li.v_hi = piv_hi;
+            job->leaves[np][bl + c] = li;
         }
+        if (overflow) set_status(ctl, TSQS_EINTERNAL);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
