@@ -123,6 +123,31 @@ void tsqs_free_storage(void);
 int tsqs_last_device_status(void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Allocation-free sort (the paper has no counterpart).
+ * For callers that cannot allocate device memory when they need a sort: programs whose
+ * device memory is owned entirely by another allocator (a framework's caching pool or a
+ * fixed arena, where a raw cudaMalloc fails or fragments it), services that account for
+ * every device byte up front, and latency-critical paths that cannot afford a cudaMalloc
+ * that may synchronise the device.  The result is the same as tsqs_sort's; all scratch
+ * lives in a static device array that is part of this library's device code
+ * (TSQS_NOALLOC_MAX_BYTES for the second buffer plus 4 MiB for the queues).  Every GPU
+ * on which that code is loaded keeps the array until the process exits.
+ *   - Sizes: nmemb * elem_size <= TSQS_NOALLOC_MAX_BYTES, else TSQS_EINVAL and nothing
+ *     is queued.  Other arguments as tsqs_sort.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device does the set-up: it looks up the array's device
+ *     address with cudaGetSymbolAddress and sets kernel attributes.  Make that first
+ *     call before any stream capture begins.
+ *   - Every call shares the one array, which keeps the previous call's contents (each
+ *     call clears what must start at zero).  Calls whose GPU work overlapped would race
+ *     on it; this entry point prevents that within a process by holding a lock for the
+ *     whole call and returning only after its sort has finished on `stream`.
+ *   - Returns the sort's device status (TSQS_OK, TSQS_ETIMEOUT, TSQS_EINTERNAL).
+ * ------------------------------------------------------------------------------- */
+#define TSQS_NOALLOC_MAX_BYTES (16u << 20)
+int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * Explicit contexts: independent scratch and graphs, e.g. one per stream.
  * ------------------------------------------------------------------------------- */
 tsqs_ctx *tsqs_ctx_create(const tsqs_plan *plan);          /* NULL plan = defaults */

@@ -735,3 +735,66 @@ int tsqs_debug_small_sort(void *base, size_t nmemb, size_t elem_size, int key_ki
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Helpers for sorts whose scratch is not owned by a context (used by the
+// allocation-free entry point in tsqs_noalloc.cu).
+// ---------------------------------------------------------------------------------
+namespace tsqs {
+
+const KindOps *host_ops(int key_kind) { return get_ops(key_kind); }
+
+// Default plan, normalised, for key_kind.
+void host_default_plan(int key_kind, tsqs_plan *p) {
+    fill_default_plan(key_kind, 0, p);
+    normalise_plan(p);
+}
+
+// Scratch bytes a single-segment sort of n elements needs under plan p.
+size_t host_scratch_bytes(const KindOps *o, const tsqs_plan &p, size_t n) {
+    return make_layout(n, 1, (size_t)o->elem_size, p, part_of(o, p).tile, o->leaf_max).total;
+}
+
+// Partition kernel shape the plan selects.
+const PartVariant &host_part(const KindOps *o, const tsqs_plan &p) { return part_of(o, p); }
+
+// Describes a single-segment sort of base[0, n) whose scratch is the caller-provided
+// block [scratch, scratch + bytes).  TSQS_ENOMEM if the block is too small.
+int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t n, char *scratch,
+                     size_t bytes, Job *j) {
+    const size_t es = (size_t)o->elem_size;
+    const Layout L = make_layout(n, 1, es, plan, part_of(o, plan).tile, o->leaf_max);
+    if (L.total > bytes) return TSQS_ENOMEM;
+    memset(j, 0, sizeof(*j));
+    const uintptr_t b = (uintptr_t)base;
+    j->base = base;
+    j->alt = scratch + L.alt_off + (b & 15u);
+    j->n = n;
+    j->seg_offsets = nullptr;
+    j->nseg = 1;
+    j->front[0] = (SegDesc *)(scratch + L.front_off[0]);
+    j->front[1] = (SegDesc *)(scratch + L.front_off[1]);
+    j->leaves[0] = (LeafItem *)(scratch + L.leaves_off[0]);
+    j->leaves[1] = (LeafItem *)(scratch + L.leaves_off[1]);
+    j->tile_seg = (uint32_t *)(scratch + L.tseg_off);
+    j->tile_status = (unsigned long long *)(scratch + L.tstat_off);
+    j->seg_done = (uint32_t *)(scratch + L.done_off);
+    j->seg_cursor = (unsigned long long *)(scratch + L.cursor_off);
+    j->cap_front = L.cap_front;
+    j->cap_tiles = L.cap_tiles;
+    j->cap_leaves = L.cap_leaves;
+    j->small_T = (uint32_t)eff_threshold(plan, o->leaf_max);
+    j->samples = (uint32_t)plan.sample_count;
+    j->vec_off = (uint32_t)((b / es) % (16 / es));
+    j->spin_limit = kDefaultSpin;
+    j->pad = 0u;
+    unsigned lg = 1;
+    while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
+    j->max_levels = 256u + 8u * lg;
+    j->offset_mode = plan.offset_mode == 1 ? 1u : 0u;
+    j->tile = (uint32_t)part_of(o, plan).tile;
+    j->seed = plan.seed;
+    return TSQS_OK;
+}
+
+}  // namespace tsqs
