@@ -659,6 +659,9 @@ __global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 
             const D pd = K::pdom(c_from<C>(m.piv_lo, m.piv_hi));
             const int64_t sb = (int64_t)m.sb, se = (int64_t)m.se;
             const bool full_tile = m.t0 >= sb && m.t0 + TILE <= se && m.cs == m.t0 && m.ce == m.t0 + TILE;
+            // tile-local bounds of the segment and of the bulk-copied range
+            const int lo = (int)max((int64_t)0, sb - m.t0), hi = (int)min((int64_t)TILE, se - m.t0);
+            const bool covered = m.cs - m.t0 <= lo && m.ce - m.t0 >= hi;
             if (full_tile) {                             // interior tile: no bounds checks
 #pragma unroll
                 for (int k = 0; k < NV; k++) lds_vec<S, V>(buf + (k * BLOCK + tid) * V, &v[k * V]);
@@ -668,7 +671,21 @@ __global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 
                     ltm |= (uint32_t)c_lt(d, pd) << i;
                     gtm |= (uint32_t)c_lt(pd, d) << i;
                 }
-            } else {                                     // segment ends or buffer ends
+            } else if (covered) {                        // segment ends inside the tile
+#pragma unroll
+                for (int k = 0; k < NV; k++) lds_vec<S, V>(buf + (k * BLOCK + tid) * V, &v[k * V]);
+#pragma unroll
+                for (int k = 0; k < NV; k++) {
+#pragma unroll
+                    for (int j = 0; j < V; j++) {
+                        const int idx = (k * BLOCK + tid) * V + j;
+                        const bool in = idx >= lo && idx < hi;
+                        const D d = K::dom(v[k * V + j]);
+                        ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
+                        gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
+                    }
+                }
+            } else {                                     // the buffer's own ends
 #pragma unroll
                 for (int k = 0; k < NV; k++) {
 #pragma unroll
@@ -808,13 +825,17 @@ __device__ __forceinline__ void cx(C &lo, C &hi) {
 
 __device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
 
-// Sorts s[0, P) ascending; P a power of two with 32 E <= P <= E * blockDim.x.  Every
-// thread of the block must call it (it contains block barriers).
+// Sorts s[0, P) ascending; P a power of two with 32 E <= P <= E * blockDim.x, and
+// s[len, P) holding the largest key.  Every thread of the block must call it (it
+// contains block barriers).  In the mirror form the padding never moves: every
+// comparator that touches it leaves both elements in place.  So a warp whose
+// elements are all padding does no work, and its shared-memory slots keep the
+// padding its partners read.
 template <class C, int E>
-__device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P) {
+__device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
     const uint32_t t = threadIdx.x, lane = t & 31u;
     const uint32_t NT = P / E;
-    const bool act = t < NT;
+    const bool act = t < NT && (t & ~31u) * (uint32_t)E < len;
     C v[E];
     if (act) {
 #pragma unroll
@@ -1030,12 +1051,12 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         } else {
             // E = min(MAXE, P / 32) keys per thread
             const uint32_t E = min((uint32_t)MAXE, P / 32u);
-            if (E == 1) bitonic_mirror<C, 1>(s, P);
-            else if (E == 2) bitonic_mirror<C, 2>(s, P);
-            else if (E == 4) bitonic_mirror<C, 4>(s, P);
-            else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P);
-            else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P);
-            else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P);
+            if (E == 1) bitonic_mirror<C, 1>(s, P, it.len);
+            else if (E == 2) bitonic_mirror<C, 2>(s, P, it.len);
+            else if (E == 4) bitonic_mirror<C, 4>(s, P, it.len);
+            else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P, it.len);
+            else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P, it.len);
+            else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P, it.len);
             for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
             sorted += it.len;
         }
