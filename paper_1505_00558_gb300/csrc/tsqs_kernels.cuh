@@ -159,9 +159,30 @@ __device__ __forceinline__ void stg_vec(S *p, const S *in) {
     *reinterpret_cast<uint4 *>(p) = u.q;
 }
 
+// Body of copy_run: nvec 16-byte destination vectors.  Destination vector q takes the
+// staged elements SH + q V .. SH + q V + V - 1 counted from the 16-byte-aligned shared
+// address sa, so it is assembled from one (SH = 0) or two aligned 16-byte shared loads
+// and no scalar shared access is needed.
+__device__ __forceinline__ uint32_t smem_addr_of(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+template <class S, int V, int NT, int SH>
+__device__ __forceinline__ void copy_body(S *__restrict__ d, const S *sa, uint32_t nvec) {
+    for (uint32_t q = threadIdx.x; q < nvec; q += NT) {
+        S a[V], b[V], o[V];
+        lds_vec<S, V>(sa + q * V, a);
+        if (SH != 0) lds_vec<S, V>(sa + q * V + V, b);
+#pragma unroll
+        for (int j = 0; j < V; j++) o[j] = (j + SH < V) ? a[j + SH] : b[j + SH - V];
+        stg_vec<S, V>(d + q * V, o);
+    }
+}
+
 // Copies cnt staged elements st[0, cnt) to dst[x, x + cnt): scalar up to the first
 // 16-byte boundary of the destination, 16-byte stores for the body, scalar tail.
-// (element x of dst is 16-byte aligned iff (x + vec_off) % V == 0)
+// (element x of dst is 16-byte aligned iff (x + vec_off) % V == 0; st lies in a
+// 16-byte-aligned shared buffer, so the vectors it reads never leave that buffer)
 template <class S, int V, int NT>
 __device__ __forceinline__ void copy_run(S *__restrict__ dst, uint64_t x, const S *st,
                                          uint32_t cnt, uint32_t vec_off) {
@@ -172,11 +193,15 @@ __device__ __forceinline__ void copy_run(S *__restrict__ dst, uint64_t x, const 
     const uint32_t body_end = head + nvec * V;
     const int t = threadIdx.x;
     if ((uint32_t)t < head) dst[x + t] = st[t];
-    for (uint32_t q = t; q < nvec; q += NT) {
-        S tmp[V];
-#pragma unroll
-        for (int j = 0; j < V; j++) tmp[j] = st[head + q * V + j];
-        stg_vec<S, V>(dst + x + head + q * V, tmp);
+    if (nvec != 0) {
+        // misalignment (in elements) of the body's first staged element
+        const uint32_t sh = (uint32_t)((smem_addr_of(st + head) / sizeof(S)) % V);
+        const S *sa = st + head - sh;
+        S *d = dst + x + head;
+        if (sh == 0) copy_body<S, V, NT, 0>(d, sa, nvec);
+        else if (V > 1 && sh == 1) copy_body<S, V, NT, (V > 1 ? 1 : 0)>(d, sa, nvec);
+        else if (V > 2 && sh == 2) copy_body<S, V, NT, (V > 2 ? 2 : 0)>(d, sa, nvec);
+        else if (V > 3) copy_body<S, V, NT, (V > 3 ? 3 : 0)>(d, sa, nvec);
     }
     const uint32_t tail = cnt - body_end;
     if ((uint32_t)t < tail) dst[x + body_end + t] = st[body_end + t];
