@@ -516,6 +516,16 @@ template <int N>
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
+// Shared-memory store through a 32-bit shared-window address.
+__device__ __forceinline__ void sts_raw(uint32_t a, unsigned int v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+__device__ __forceinline__ void sts_raw(uint32_t a, unsigned long long v) {
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v));
+}
+__device__ __forceinline__ void sts_raw(uint32_t a, Rec16 v) {
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(v.key), "l"(v.pay));
+}
 __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
     uint32_t old;
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -693,8 +703,8 @@ __global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 
 #pragma unroll
                 for (int i = 0; i < ITEMS; i++) {
                     const D d = K::dom(v[i]);
-                    ltm |= (uint32_t)c_lt(d, pd) << i;
-                    gtm |= (uint32_t)c_lt(pd, d) << i;
+                    if (c_lt(d, pd)) ltm |= 1u << i;
+                    if (c_lt(pd, d)) gtm |= 1u << i;
                 }
             } else if (covered) {                        // segment ends inside the tile
 #pragma unroll
@@ -764,13 +774,17 @@ __global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 
                 resv = atomicAdd(job->seg_cursor + m.si, (unsigned long long)((agg_gt << 32) | agg_lt));
             // stage without branches: <p from the front, >p from the back, =p (and
             // elements outside the segment) into the dummy slot at TILE
-            uint32_t lp = texcl & 0xFFFFu, gp = (TILE - 1) - (texcl >> 16);
+            // (32-bit shared-window addresses keep the address arithmetic to one add)
+            const uint32_t b0 = smem_addr(buf), es = (uint32_t)sizeof(S);
+            uint32_t la = b0 + (texcl & 0xFFFFu) * es;
+            uint32_t ga = b0 + ((TILE - 1) - (texcl >> 16)) * es;
+            const uint32_t da = b0 + (uint32_t)TILE * es;
 #pragma unroll
             for (int k = 0; k < ITEMS; k++) {
-                const uint32_t l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
-                buf[l ? lp : (g ? gp : (uint32_t)TILE)] = v[k];
-                lp += l;
-                gp -= g;
+                const bool l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
+                sts_raw(l ? la : (g ? ga : da), v[k]);
+                la += l ? es : 0u;
+                ga -= g ? es : 0u;
             }
             if (warp == 0 && job->offset_mode != 0u) {
                 // look-back mode: publish the aggregate, walk back, publish the inclusive
@@ -840,6 +854,13 @@ __device__ __forceinline__ U128 c_shfl_xor(U128 v, int m) {
     return U128{__shfl_xor_sync(0xffffffffu, v.lo, m), __shfl_xor_sync(0xffffffffu, v.hi, m)};
 }
 
+// One side of a comparator whose partner value w lives in another thread or in shared
+// memory: the lower side keeps the minimum, the upper side the maximum.
+template <class C>
+__device__ __forceinline__ C cx_side(C v, C w, bool lower) {
+    return (c_lt(w, v) == lower) ? w : v;
+}
+
 // min to the lower index, max to the upper
 template <class C>
 __device__ __forceinline__ void cx(C &lo, C &hi) {
@@ -892,9 +913,9 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
                     const C wa = c_shfl_xor(v[E - 1 - r], lm);
                     if (r != E - 1 - r) {
                         const C wb = c_shfl_xor(v[r], lm);
-                        v[E - 1 - r] = lower ? c_min(v[E - 1 - r], wb) : c_maxv(v[E - 1 - r], wb);
+                        v[E - 1 - r] = cx_side(v[E - 1 - r], wb, lower);
                     }
-                    v[r] = lower ? c_min(v[r], wa) : c_maxv(v[r], wa);
+                    v[r] = cx_side(v[r], wa, lower);
                 }
             }
         } else {                                         // across warps: shared memory
@@ -909,7 +930,7 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
 #pragma unroll
                 for (int r = 0; r < E; r++) {
                     const C w = s[pad32((t * E + r) ^ (k - 1))];
-                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
+                    v[r] = cx_side(v[r], w, lower);
                 }
             }
         }
@@ -926,7 +947,7 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
 #pragma unroll
                 for (int r = 0; r < E; r++) {
                     const C w = s[pad32((t * E + r) ^ j)];
-                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
+                    v[r] = cx_side(v[r], w, lower);
                 }
             }
         }
@@ -938,7 +959,7 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
 #pragma unroll
                 for (int r = 0; r < E; r++) {
                     const C w = c_shfl_xor(v[r], lm);
-                    v[r] = lower ? c_min(v[r], w) : c_maxv(v[r], w);
+                    v[r] = cx_side(v[r], w, lower);
                 }
             }
             // ---- half-cleaners inside the thread
