@@ -26,8 +26,8 @@ KindOps make_ops() {
     o.pivot_block = kPivotBlock;
     o.leaf_smem = (int)LeafLayout<KIND>::bytes;
     o.leaf_max = kMaxSmall;
-    o.part[0] = part_variant<KIND, 256, 16, 3>();
-    o.part[1] = part_variant<KIND, 256, 16, 4>();
+    o.part[0] = part_variant<KIND, 256, 32, 3>();
+    o.part[1] = part_variant<KIND, 256, 16, 3>();
     o.part[2] = part_variant<KIND, 512, 16, 2>();
     o.part[3] = part_variant<KIND, 128, 16, 4>();
     o.k_init = (const void *)k_init<KIND>;

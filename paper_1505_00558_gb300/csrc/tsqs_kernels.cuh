@@ -573,7 +573,7 @@ struct PartMisc {
 };
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
-__global__ void __launch_bounds__(BLOCK + 32, (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 8))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
+__global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 : 4) : (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 8)))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
@@ -951,9 +951,42 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
                 }
             }
         }
+        // the transposed lane stages below reuse this warp's stretch of the buffer,
+        // which other warps read in a shared-memory stage just above
+        if constexpr (E == 32) if (k > 32u * E) __syncthreads();
         if (act) {
             // ---- half-cleaners across lanes
-            for (uint32_t j = min(k >> 2, 16u * E); j >= (uint32_t)E; j >>= 1) {
+            uint32_t jl = min(k >> 2, 16u * E);
+            if constexpr (E == 32) if (jl >= 4u * E) {
+                // Three to five lane strides in a row: transpose the warp's 32 x 32 block
+                // (lane <-> register) through its own stretch of the padded buffer, run the
+                // strides as in-register comparators, transpose back.  In the padded
+                // layout element (lane l, register r) of warp w sits at w*1056 + l*33 + r,
+                // so both directions are free of bank conflicts.  Lane l writes and later
+                // reads row l, and in between reads and writes column l, so the two
+                // __syncwarp calls order every cross-lane access.
+                C *wb = s + (t >> 5) * (32u * 33u);
+#pragma unroll
+                for (int r = 0; r < E; r++) wb[lane * 33u + r] = v[r];
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < E; r++) v[r] = wb[r * 33u + lane];
+#pragma unroll
+                for (int rs = 16; rs >= 1; rs >>= 1) {
+                    if ((uint32_t)rs * (uint32_t)E <= jl) {
+#pragma unroll
+                        for (int r = 0; r < E; r++)
+                            if ((r & rs) == 0) cx(v[r], v[r | rs]);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < E; r++) wb[r * 33u + lane] = v[r];
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < E; r++) v[r] = wb[lane * 33u + r];
+                jl = 0;                                  // lane strides done
+            }
+            for (uint32_t j = jl; j >= (uint32_t)E; j >>= 1) {
                 const int lm = (int)(j / E);
                 const bool lower = (lane & (uint32_t)lm) == 0u;
 #pragma unroll

@@ -7,8 +7,9 @@ x0 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", 201
 x0 is derived from (seed, tag) with the same finaliser.
 
 The seven orderings follow the paper's test inputs (Section VI: random, sorted,
-reversed, organ pipes, many equals, stair steps, nearly sorted); the records and
-floats follow the workload recipe stated in the design doc.
+reversed, organ pipes, many equals, stair steps, nearly sorted).  Records are 64-bit
+keys with 64-bit payloads and some duplicated keys and records; floats are normal
+draws with +-0, +-inf and NaNs of both signs mixed in.
 """
 from __future__ import annotations
 
