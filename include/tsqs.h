@@ -70,7 +70,7 @@ typedef struct {
                                   capped per kind at 4096 (4-byte), 2048 (8-byte), 1024
                                   (records): the largest leaf one warp holds in registers */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
-    int32_t  sample_count;     /* pivot sample size: 15, 31 or 63                      */
+    int32_t  sample_count;     /* pivot sample size (odd, at most 63; default 31)       */
     int32_t  offset_mode;      /* where a tile writes its <p and >p runs:
                                   0 = reserved with one 64-bit atomic on a per-segment
                                       cursor (default; tiles never wait on each other),
@@ -192,9 +192,10 @@ int tsqs_ctx_sort_timed(tsqs_ctx *ctx, void *base, size_t nmemb, size_t elem_siz
  * Step-level entry points (used to test each kernel alone against the oracle).
  * ------------------------------------------------------------------------------- */
 
-/* Pivot kernel on one segment [seg_begin, seg_end) of base: writes the sample
- * positions it used (sample_count uint64, host) and the pivot element (elem_size
- * bytes, host, original representation).  Synchronises `stream`. */
+/* Pivot kernel on one segment [seg_begin, seg_end) of base with exactly sample_count
+ * samples (at most 63; clamped to the segment length and made odd): writes the
+ * sample positions it used (h_positions holds sample_count uint64, host) and the pivot
+ * element (elem_size bytes, host, original representation).  Synchronises `stream`. */
 int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_kind,
                      uint64_t seg_begin, uint64_t seg_end, int sample_count, uint64_t seed,
                      uint64_t *h_positions, void *h_pivot, void *stream);

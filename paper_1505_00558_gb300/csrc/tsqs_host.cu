@@ -682,8 +682,10 @@ int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_k
     CK(cudaMemcpyAsync(pos, d_pos, sizeof(pos), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h_pivot, d_piv, elem_size, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    uint32_t S = j.samples > (uint32_t)kMaxSamples ? (uint32_t)kMaxSamples : j.samples;
-    for (uint32_t i = 0; i < (uint32_t)kMaxSamples; i++) h_positions[i] = i < S ? pos[i] : ~0ull;
+    // the kernel draws min(sample_count, segment length) samples, made odd; the caller's
+    // array holds sample_count entries, and unused ones read as all ones
+    const uint32_t S = j.samples > (uint32_t)kMaxSamples ? (uint32_t)kMaxSamples : j.samples;
+    for (uint32_t i = 0; i < S; i++) h_positions[i] = pos[i];
     CK(cudaEventRecord(c->done_ev, s));
     c->ev_valid = true;
     return TSQS_OK;

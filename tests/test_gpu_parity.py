@@ -165,8 +165,10 @@ def test_pivot_kernel_is_lower_median_of_its_sample(T, orc):
     n = 1_000_003
     a = int32_pattern("random", n, seed=6)
     t = to_dev(a)
-    for (b, e, S) in [(0, n, 31), (17, 100_017, 63), (5000, 9100, 15), (123, 4220, 31)]:
-        pos = (ctypes.c_uint64 * 63)()
+    for (b, e, S) in [(0, n, 31), (17, 100_017, 63), (5000, 9100, 15), (123, 4220, 31),
+                      (40, 140, 63), (7, 38, 63), (3, 4, 31)]:
+        pos = (ctypes.c_uint64 * S)()
+        S = min(S, e - b) - (1 - min(S, e - b) % 2)
         piv = np.zeros(1, np.int32)
         rc = T.lib().tsqs_debug_pivot(ctypes.c_void_p(t.data_ptr()), n, 4, 1, b, e, S, 77, pos,
                                       ctypes.c_void_p(piv.ctypes.data), None)
