@@ -53,16 +53,18 @@ size_t kind_size(int kind) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t alt_off, front_off[2], leaves_off[2], tseg_off, tstat_off, done_off, cursor_off, misc_off, total;
-    uint32_t cap_front, cap_tiles, cap_leaves;
+    size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, misc_off, total;
+    uint32_t cap_front, cap_tiles, cap_leaves, leaf_defer;
 };
 
 // Scratch needed for nmemb elements in nseg segments (bounds, not estimates):
 //   frontier  segments above small_T in one level are disjoint: <= n/(T+1) (+ nseg for
 //             the step-level partition test, which seeds every given segment)
 //   tiles     <= n/TILE + 2 per segment (partial first and last tiles)
-//   leaves    <= 2 children per partitioned segment, n/kFillChunk + 1 fill items per
-//             segment, plus the small root segments
+//   leaves    one level adds <= 2 children per partitioned segment, n/kFillChunk + 1
+//             fill items per segment, plus the small root segments: cl.  Items queue up
+//             across levels; a level's leaf pass runs once more than cl are queued, so
+//             the queue never holds more than 2 cl
 // Effective on-chip threshold: the plan's, capped by what the kind's leaf kernel holds.
 size_t eff_threshold(const tsqs_plan &plan, int leaf_max) {
     return std::min<size_t>((size_t)plan.small_threshold, (size_t)leaf_max);
@@ -76,13 +78,13 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     const size_t cl = 3 * cf + n / kFillChunk + nseg + 4;
     L.cap_front = (uint32_t)std::min<size_t>(cf, 0xFFFFFFF0u);
     L.cap_tiles = (uint32_t)std::min<size_t>(ct, 0xFFFFFFF0u);
-    L.cap_leaves = (uint32_t)std::min<size_t>(cl, 0xFFFFFFF0u);
+    L.cap_leaves = (uint32_t)std::min<size_t>(2 * cl, 0xFFFFFFF0u);
+    L.leaf_defer = (uint32_t)std::min<size_t>(cl, 0x7FFFFFF0u);
     size_t off = 0;
     L.alt_off = off;            off = align_up(off + n * es + 16, 256);
     L.front_off[0] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
     L.front_off[1] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
-    L.leaves_off[0] = off;      off = align_up(off + cl * sizeof(LeafItem), 256);
-    L.leaves_off[1] = off;      off = align_up(off + cl * sizeof(LeafItem), 256);
+    L.leaves_off = off;         off = align_up(off + 2 * cl * sizeof(LeafItem), 256);
     L.tseg_off = off;           off = align_up(off + ct * sizeof(uint32_t), 256);
     L.tstat_off = off;          off = align_up(off + ct * sizeof(unsigned long long), 256);
     L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
@@ -228,8 +230,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->nseg = offs ? nseg : 1;
     j->front[0] = (SegDesc *)(c->scratch + L.front_off[0]);
     j->front[1] = (SegDesc *)(c->scratch + L.front_off[1]);
-    j->leaves[0] = (LeafItem *)(c->scratch + L.leaves_off[0]);
-    j->leaves[1] = (LeafItem *)(c->scratch + L.leaves_off[1]);
+    j->leaves = (LeafItem *)(c->scratch + L.leaves_off);
     j->tile_seg = (uint32_t *)(c->scratch + L.tseg_off);
     j->tile_status = (unsigned long long *)(c->scratch + L.tstat_off);
     j->seg_done = (uint32_t *)(c->scratch + L.done_off);
@@ -237,6 +238,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
+    j->leaf_defer = L.leaf_defer;
     j->small_T = (uint32_t)eff_threshold(c->plan, o->leaf_max);
     j->samples = (uint32_t)c->plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));
@@ -280,13 +282,16 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     CK(cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
-    cudaGraphNode_t n_leaf, n_piv, n_part, n_fin;
+    cudaGraphNode_t n_leaf, n_piv, n_part, n_fin, n_last;
+    int leaf_final = 0, leaf_last = 1;
+    void *argsl[] = {&pj, &pc, &leaf_final};
+    void *argsl_last[] = {&pj, &pc, &leaf_last};
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_leaf;
     kp.gridDim = dim3(c->leaf_grid[k]);
     kp.blockDim = dim3(o->leaf_block);
     kp.sharedMemBytes = (unsigned)o->leaf_smem;
-    kp.kernelParams = args2;
+    kp.kernelParams = argsl;
     CK(cudaGraphAddKernelNode(&n_leaf, body, nullptr, 0, &kp));
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_pivot;
@@ -311,6 +316,14 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.blockDim = dim3(128);
     kp.kernelParams = argsf;
     CK(cudaGraphAddKernelNode(&n_fin, body, &n_part, 1, &kp));
+    // the final leaf pass, after the loop
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_leaf;
+    kp.gridDim = dim3(c->leaf_grid[k]);
+    kp.blockDim = dim3(o->leaf_block);
+    kp.sharedMemBytes = (unsigned)o->leaf_smem;
+    kp.kernelParams = argsl_last;
+    CK(cudaGraphAddKernelNode(&n_last, g, &n_loop, 1, &kp));
 
     cudaGraphExec_t ex = nullptr;
     CK(cudaGraphInstantiate(&ex, g, 0));
@@ -597,6 +610,9 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     int use_h = 0;
     unsigned int unused = 0;
     void *argsf[] = {&pj, &pc, &h, &use_h, &unused};
+    int leaf_final = 0, leaf_last = 1;
+    void *argsl[] = {&pj, &pc, &leaf_final};
+    void *argsl_last[] = {&pj, &pc, &leaf_last};
     cudaEvent_t ev[4];
     for (auto &e : ev) CK(cudaEventCreate(&e));
     k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
@@ -604,7 +620,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     int L = 0;
     for (;;) {
         CK(cudaEventRecord(ev[2], s));
-        CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), args2,
+        CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl,
                             (size_t)o->leaf_smem, s));
         CK(cudaEventRecord(ev[3], s));
         CK(cudaLaunchKernel(o->k_pivot, dim3(c->sms * 4), dim3(o->pivot_block), args2, 0, s));
@@ -626,6 +642,17 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
         L++;
         if (!*c->h_cont) break;
         if (L > 100000) break;
+    }
+    // final leaf pass; its time is added to the last level's leaf entry
+    CK(cudaEventRecord(ev[2], s));
+    CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl_last,
+                        (size_t)o->leaf_smem, s));
+    CK(cudaEventRecord(ev[3], s));
+    CK(cudaStreamSynchronize(s));
+    if (L >= 1 && L - 1 < max_levels && h_leaf_ms) {
+        float lms = 0.f;
+        CK(cudaEventElapsedTime(&lms, ev[2], ev[3]));
+        h_leaf_ms[L - 1] += lms;
     }
     for (auto &e : ev) cudaEventDestroy(e);
     if (h_keys) {
@@ -776,8 +803,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     j->nseg = 1;
     j->front[0] = (SegDesc *)(scratch + L.front_off[0]);
     j->front[1] = (SegDesc *)(scratch + L.front_off[1]);
-    j->leaves[0] = (LeafItem *)(scratch + L.leaves_off[0]);
-    j->leaves[1] = (LeafItem *)(scratch + L.leaves_off[1]);
+    j->leaves = (LeafItem *)(scratch + L.leaves_off);
     j->tile_seg = (uint32_t *)(scratch + L.tseg_off);
     j->tile_status = (unsigned long long *)(scratch + L.tstat_off);
     j->seg_done = (uint32_t *)(scratch + L.done_off);
@@ -785,6 +811,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
+    j->leaf_defer = L.leaf_defer;
     j->small_T = (uint32_t)eff_threshold(plan, o->leaf_max);
     j->samples = (uint32_t)plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));

@@ -3,9 +3,12 @@
 // One sort is a level-synchronous walk over a device-built work queue:
 //   frontier[par]  segments larger than the small threshold waiting for a partition
 //                  level (the recursion of Fig. 1 turned into a breadth-first queue);
-//   leaves[par]    work for the on-chip pass: segments of <= small threshold elements
+//   leaves         work for the on-chip pass: segments of <= small threshold elements
 //                  to sort (Section IV's role) and runs of =p to fill with p
 //                  (Section III.F: the equals are placed once and never compared again).
+//                  Items of every level queue up (each remembers the buffer holding its
+//                  keys; no later level touches its range) and run in one pass after
+//                  the level loop, or earlier only if the queue would overflow.
 // Level L reads buffer L%2 (0 = caller's array, 1 = scratch) and writes buffer
 // (L+1)%2; every element reaches its final place in the caller's array exactly once,
 // through a leaf sort or an =p fill.
@@ -20,6 +23,8 @@ constexpr int kMaxSmall = 4096;             // largest on-chip segment
 constexpr int kStatLevels = 64;
 
 enum LeafKind : uint32_t { LEAF_SORT = 0, LEAF_FILL = 1 };
+// LeafItem::kind flag: the item's keys are in buffer 1 (alt) rather than buffer 0
+constexpr uint32_t kLeafInAlt = 0x100u;
 
 // A segment [begin, end) waiting for a partition level.
 struct SegDesc {
@@ -33,7 +38,7 @@ struct SegDesc {
 struct LeafItem {
     uint64_t begin;
     uint32_t len;
-    uint32_t kind;            // LeafKind
+    uint32_t kind;            // LeafKind, | kLeafInAlt for a sort whose keys are in alt
     uint64_t v_lo, v_hi;      // canonical fill value for LEAF_FILL
 };
 
@@ -42,12 +47,13 @@ struct Ctl {
     uint32_t level;           // current level (iteration of the level loop)
     uint32_t status;          // sticky tsqs_status of the device side
     uint32_t tile_claim;      // partition tiles claimed in this level
-    uint32_t leaf_claim;      // leaf items claimed in this level
+    uint32_t leaf_claim;      // leaf items claimed by the running leaf pass
     uint32_t seg_claim;       // frontier segments claimed by the pivot kernel
     uint32_t cont;            // level loop continues (host-driven mode reads it)
     uint32_t nfront[2];
     uint32_t ntiles[2];
-    uint32_t nleaf[2];
+    uint32_t nleaf;           // leaf items queued (across levels, until a leaf pass)
+    uint32_t leaf_blocks;     // leaf-pass blocks finished (last one empties the queue)
     uint32_t max_front;
     uint32_t levels_done;
     uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
@@ -66,12 +72,13 @@ struct Job {
     const uint64_t *seg_offsets;   // nullptr: one segment [0, n)
     uint64_t nseg;
     SegDesc *front[2];
-    LeafItem *leaves[2];
+    LeafItem *leaves;         // leaf items of every level since the last leaf pass
     uint32_t *tile_seg;       // tile id -> frontier index, current level
     unsigned long long *tile_status;   // decoupled look-back words, current level
     uint32_t *seg_done;       // finished tiles per frontier segment
     unsigned long long *seg_cursor;    // reserved (#<p | #>p << 32) per frontier segment
     uint32_t cap_front, cap_tiles, cap_leaves;
+    uint32_t leaf_defer;      // a level's leaf pass runs only above this many queued items
     uint32_t small_T;         // on-chip threshold
     uint32_t samples;         // pivot sample count (odd, <= kMaxSamples)
     uint32_t vec_off;         // (address of base / elem_size) mod (16 / elem_size)

@@ -1,7 +1,7 @@
 // tsqs_kernels.cuh -- device code of the three-way partition sort (sm_103a).
 //
 // Kernels of one level of the level loop (see tsqs_internal.h for the queue layout):
-//   k_leaf       on-chip pass over the leaf items produced by the previous level:
+//   k_leaf       on-chip pass over the queued leaf items of the levels so far:
 //                sorts segments of <= small_T elements in shared memory (the role of
 //                the insertion sort of Section IV) and fills =p runs (Section III.F)
 //   k_pivot      sampled median of every frontier segment (Section III.H, V.C) and
@@ -298,11 +298,12 @@ __device__ void push_segment(const Job *job, Ctl *ctl, int np, uint64_t b, uint6
         job->front[np][fi] = d;
         atomicAdd((unsigned long long *)&ctl->front_keys[np], (unsigned long long)m);
     } else {
-        const uint32_t li = atomicAdd(&ctl->nleaf[np], 1u);
+        const uint32_t li = atomicAdd(&ctl->nleaf, 1u);
         if (li >= job->cap_leaves) { set_status(ctl, TSQS_EINTERNAL); return; }
         LeafItem it;
-        it.begin = b; it.len = (uint32_t)m; it.kind = LEAF_SORT; it.v_lo = 0; it.v_hi = 0;
-        job->leaves[np][li] = it;
+        it.begin = b; it.len = (uint32_t)m; it.kind = LEAF_SORT | (np ? kLeafInAlt : 0u);
+        it.v_lo = 0; it.v_hi = 0;
+        job->leaves[li] = it;
     }
 }
 
@@ -573,7 +574,7 @@ struct PartMisc {
 };
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
-__global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 : 4) : (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 8)))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
+__global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 : 4) : (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 6)))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
@@ -779,12 +780,25 @@ __global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 :
             uint32_t la = b0 + (texcl & 0xFFFFu) * es;
             uint32_t ga = b0 + ((TILE - 1) - (texcl >> 16)) * es;
             const uint32_t da = b0 + (uint32_t)TILE * es;
+            constexpr uint32_t kAll = ITEMS == 32 ? 0xFFFFFFFFu : ((1u << ITEMS) - 1u);
+            if (ltm == kAll || gtm == kAll) {
+                // all of this thread's keys go to one run (ordered input): write them
+                // permuted by the lane inside the thread's own stretch of the run, so
+                // that a warp's store covers 32 banks instead of one
+                const uint32_t rot = (lane & (uint32_t)(ITEMS - 1)) * es;
+                const uint32_t base = ltm == kAll ? la : ga;
+                const int sgn = ltm == kAll ? 1 : -1;
 #pragma unroll
-            for (int k = 0; k < ITEMS; k++) {
-                const bool l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
-                sts_raw(l ? la : (g ? ga : da), v[k]);
-                la += l ? es : 0u;
-                ga -= g ? es : 0u;
+                for (int k = 0; k < ITEMS; k++)
+                    sts_raw(base + sgn * (int)(((uint32_t)k * es) ^ rot), v[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < ITEMS; k++) {
+                    const bool l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
+                    sts_raw(l ? la : (g ? ga : da), v[k]);
+                    la += l ? es : 0u;
+                    ga -= g ? es : 0u;
+                }
             }
             if (warp == 0 && job->offset_mode != 0u) {
                 // look-back mode: publish the aggregate, walk back, publish the inclusive
@@ -838,8 +852,11 @@ __global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 :
 // compares element i with i ^ (k - 1), then runs half-cleaners i vs i ^ j
 // (j = k/4 .. 1), and every comparator puts the minimum at the lower index, so all
 // in-thread comparators have compile-time directions.  Strides below E stay inside a
-// thread, strides below 32 E cross lanes through __shfl_xor_sync, larger strides go
-// through shared memory (one pad word per 32 keeps the accesses conflict-free).
+// thread, strides below 32 E cross lanes through __shfl_xor_sync (with E = 32, a run of
+// three to five such strides runs in registers between two warp-local transposes),
+// larger strides go through shared memory (one pad word per 32 keeps the accesses
+// conflict-free).  Items queue up across levels and run in as few passes as the queue
+// capacity allows: normally one, after the level loop.
 // ---------------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned int c_min(unsigned int a, unsigned int b) { return min(a, b); }
@@ -1026,7 +1043,7 @@ struct LeafLayout {
 };
 
 template <int KIND, int LB, int MAXE, int MINB>
-__global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, Ctl *ctl) {
+__global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, Ctl *ctl, int final_pass) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
@@ -1040,10 +1057,13 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     __shared__ LeafItem s_it[2];
     __shared__ int64_t s_cs[2], s_ce[2];
     __shared__ uint32_t s_ok[2];
-    const int par = ctl->level & 1;
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
-    const uint32_t nl = min(ctl->nleaf[par], job->cap_leaves);
-    const S *src = buffer<K>(job, par);          // may be the same buffer as out
+    // Leaf items queue up across levels (their ranges are never touched by a later
+    // partition); a level's pass runs only when the queue would otherwise outgrow its
+    // capacity, and one final pass after the level loop runs the rest.  nleaf does not
+    // change while this kernel runs, so every block takes the same decision.
+    const uint32_t nl = min(ctl->nleaf, job->cap_leaves);
+    if (!final_pass && nl <= job->leaf_defer) return;
     S *out = reinterpret_cast<S *>(job->base);
     const int64_t n = (int64_t)job->n;
     const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
@@ -1054,11 +1074,12 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     auto claim = [&](int slot) {
         const uint32_t ii = atomicAdd(&ctl->leaf_claim, 1u);
         if (ii >= nl) { s_ok[slot] = 0u; return; }
-        const LeafItem it = job->leaves[par][ii];
+        const LeafItem it = job->leaves[ii];
         s_it[slot] = it;
         s_ok[slot] = 1u;
         s_cs[slot] = s_ce[slot] = 0;
-        if (it.kind == LEAF_SORT && it.len <= (uint32_t)kMaxSmall) {
+        if ((it.kind & 0xFFu) == LEAF_SORT && it.len <= (uint32_t)kMaxSmall) {
+            const S *src = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0);
             const int64_t b = (int64_t)it.begin, e = b + it.len;
             const int64_t cs = max(b - ((b + (int64_t)job->vec_off) % V), e_lo);
             const int64_t ce = min(e + ((V - ((e + (int64_t)job->vec_off) % V)) % V), e_hi);
@@ -1087,7 +1108,9 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         const LeafItem it = s_it[sl];
         const int64_t cs = s_cs[sl], ce = s_ce[sl];
         items++;
-        const bool is_sort = it.kind != LEAF_FILL && it.len <= (uint32_t)kMaxSmall;
+        const bool is_fill = (it.kind & 0xFFu) == LEAF_FILL;
+        const bool is_sort = !is_fill && it.len <= (uint32_t)kMaxSmall;
+        const S *src = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0);   // may equal out
         uint32_t P = 32;
         if (is_sort) {
             if (ce > cs) {
@@ -1112,7 +1135,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         fence_proxy_async();                // this slot's reads precede its next bulk copy
         __syncthreads();                    // sort buffer loaded, slot free, s_it read
         if (threadIdx.x == 0) claim(sl ^ 1);            // prefetch the next item meanwhile
-        if (it.kind == LEAF_FILL) {
+        if (is_fill) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
             S rep[V];
 #pragma unroll
@@ -1145,6 +1168,16 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         atomicAdd((unsigned long long *)&ctl->leaf_sorted, (unsigned long long)sorted);
         atomicAdd((unsigned long long *)&ctl->leaf_filled, (unsigned long long)filled);
         atomicAdd((unsigned long long *)&ctl->leaf_items, (unsigned long long)items);
+    }
+    // the last block to finish empties the queue (every block has read nleaf and made
+    // its last claim by then)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->leaf_blocks, 1u) + 1u == gridDim.x) {
+            ctl->nleaf = 0u;
+            ctl->leaf_claim = 0u;
+            ctl->leaf_blocks = 0u;
+        }
     }
 }
 
@@ -1205,13 +1238,11 @@ __device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGrap
     if (ctl->nfront[par]) ctl->levels_done++;
     ctl->nfront[par] = 0u;
     ctl->ntiles[par] = 0u;
-    ctl->nleaf[par] = 0u;
     ctl->front_keys[par] = 0ull;
     ctl->tile_claim = 0u;
-    ctl->leaf_claim = 0u;
     ctl->seg_claim = 0u;
     ctl->level = L + 1;
-    const bool more = (ctl->nfront[par ^ 1] | ctl->nleaf[par ^ 1]) != 0u;
+    const bool more = ctl->nfront[par ^ 1] != 0u;    // queued leaves wait for a leaf pass
     if (more && L + 1 >= job->max_levels) set_status(ctl, TSQS_EINTERNAL);
     const uint32_t cont = (ctl->status == 0u && more) ? 1u : 0u;
     ctl->cont = cont;
@@ -1295,7 +1326,7 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
         if (lane == 31) {
             bf = atomicAdd(&ctl->nfront[np], xf);
             bt = atomicAdd(&ctl->ntiles[np], xt);
-            bl = atomicAdd(&ctl->nleaf[np], xl);
+            bl = atomicAdd(&ctl->nleaf, xl);
             if (ksum) atomicAdd((unsigned long long *)&ctl->front_keys[np], (unsigned long long)ksum);
         }
         bf = __shfl_sync(0xffffffffu, bf, 31) + xf - nfr;
@@ -1320,8 +1351,10 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
                 if (bl >= job->cap_leaves) overflow = true;
                 else {
                     LeafItem it;
-                    it.begin = cb[c]; it.len = (uint32_t)msz; it.kind = LEAF_SORT; it.v_lo = 0; it.v_hi = 0;
-                    job->leaves[np][bl] = it;
+                    it.begin = cb[c]; it.len = (uint32_t)msz;
+                    it.kind = LEAF_SORT | (np ? kLeafInAlt : 0u);     // written by this level
+                    it.v_lo = 0; it.v_hi = 0;
+                    job->leaves[bl] = it;
                 }
                 bl++;
             }
@@ -1335,7 +1368,7 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
             li.kind = LEAF_FILL;
             li.v_lo = piv_lo;
             li.v_hi = piv_hi;
-            job->leaves[np][bl + c] = li;
+            job->leaves[bl + c] = li;
         }
         if (overflow) set_status(ctl, TSQS_EINTERNAL);
     }

@@ -120,13 +120,16 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
     int use_h = 0;
     unsigned int unused = 0;
     void *argsf[] = {&pj, &pc, &h, &use_h, &unused};
+    int leaf_final = 0, leaf_last = 1;
+    void *argsl[] = {&pj, &pc, &leaf_final};
+    void *argsl_last[] = {&pj, &pc, &leaf_last};
     // setup zeroes the control block, so nothing a previous call left in the shared
     // arrays is read before it is rewritten
     k_setup<<<1, 256, 0, s>>>(d.job, d.ctl, j);
     if (cudaGetLastError() != cudaSuccess) return TSQS_ECUDA;
     if (cudaLaunchKernel(o->k_init, dim3(d.sms * 2), dim3(256), args2, 0, s) != cudaSuccess) return TSQS_ECUDA;
     for (uint32_t level = 0; level <= j.max_levels; level++) {
-        if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), args2,
+        if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl,
                              (size_t)o->leaf_smem, s) != cudaSuccess ||
             cudaLaunchKernel(o->k_pivot, dim3(d.sms * 4), dim3(o->pivot_block), args2, 0, s) != cudaSuccess ||
             cudaLaunchKernel(pv.k_partition, dim3(d.part_grid[key_kind]), dim3(pv.threads), args2,
@@ -140,6 +143,10 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
             return TSQS_ECUDA;
         if (!g_cont[dev]) break;
     }
+    // the final leaf pass over every queued item
+    if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl_last,
+                         (size_t)o->leaf_smem, s) != cudaSuccess)
+        return TSQS_ECUDA;
     uint32_t status = 0;
     if (cudaMemcpyAsync(&status, &d.ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
