@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--n", type=int, default=N_HEADLINE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lookback", action="store_true",
+                    help="with --profile: decoupled look-back offsets, whose layout (and so the "
+                         "level count) does not depend on timing")
+    ap.add_argument("--profile", action="store_true",
+                    help="one instrumented (host-driven, one launch per kernel) sort of the "
+                         "uniform workload and nothing else: the case the ncu captures use")
     return ap.parse_args()
 
 
@@ -70,6 +76,10 @@ def p_min(n: int, T: int = SMALL_T) -> int:
     """Unavoidable passes of a perfect-median three-way quicksort that finishes parts
     of <= T on chip: ceil(log2(n / T)) partition levels plus one on-chip pass."""
     return max(0, math.ceil(math.log2(n / T))) + 1 if n > T else 1
+
+
+def size_label(n: int) -> str:
+    return f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
 
 
 def kernels_sha() -> str:
@@ -268,6 +278,34 @@ def time_sorts(torch, T, copies, kind, warmup, dist, records=False):
     return total, per
 
 
+def profile_case(args, dist):
+    """One instrumented sort (every kernel its own launch: leaf, pivot, partition and
+    level end per level, then the final leaf pass), for ncu captures; the graph path
+    runs the same kernels as nodes of a conditional graph, which ncu does not profile
+    one by one."""
+    import torch
+    torch.cuda.set_device(dist.local)
+    import paper_1505_00558_gb300 as T
+    from workloads import int32_pattern
+    n = args.n
+    src = torch.from_numpy(int32_pattern("random", n, seed=1)).cuda()
+    plan = T.Plan()
+    T.lib().tsqs_plan_default(T.TSQS_I32, n, ctypes.byref(plan))
+    plan.offset_mode = 1 if args.lookback else 0
+    ctx = T.Context(plan)
+    ms, keys, lms = ctx.sort_timed(src, kind=T.TSQS_I32)
+    torch.cuda.synchronize()
+    ok = ctx.status() == 0 and bool((src[1:] >= src[:-1]).all().item())
+    if dist.rank == 0:
+        print(json.dumps({"profile_case": f"{size_label(n)} int32 uniform random seed 1",
+                          "levels": len(ms), "leaf_launches": len(ms) + 1, "sorted": ok,
+                          "partition_ms": [round(m, 4) for m in ms],
+                          "leaf_ms": [round(m, 4) for m in lms]}), flush=True)
+    ctx.close()
+    if not ok:
+        raise SystemExit(1)
+
+
 def gpu_arm(args, dist):
     import torch
     torch.cuda.set_device(dist.local)
@@ -293,13 +331,14 @@ def gpu_arm(args, dist):
     value = keys_all / (total_ms * 1e-3) / 1e6
     ms_step = total_ms / K
 
-    # launches per sort: setup + init + 4 per level iteration (leaf, pivot, partition, finish)
+    # launches per sort: setup + init + 4 per level iteration (leaf, pivot, partition,
+    # level end) + the final leaf pass
     ctx = T.Context()
     chk = src.clone()
     T.sort_(chk, kind=T.TSQS_I32, ctx=ctx)
     st = ctx.stats()
-    iters = len(st["level_keys"]) if st["level_keys"] else st["levels"] + 1
-    launches_per_sort = 2 + 4 * iters
+    iters = max(1, st["levels"])
+    launches_per_sort = 3 + 4 * iters
     del copies
 
     # dominant kernel: partition levels, timed one launch at a time with CUDA events
@@ -373,7 +412,7 @@ def gpu_arm(args, dist):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": K, "warmup": W, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "2^27 int32 uniform random [-2^31, 2^31), seed 1, tsqs_sort",
+            "config": {"workload": f"{size_label(n)} int32 uniform random [-2^31, 2^31), seed 1, tsqs_sort",
                        "n": n, "parallelism": f"replicas x{dist.world}",
                        "l2": "inputs larger than L2: every step sorts its own fresh 512 MiB copy",
                        "small_threshold": SMALL_T},
@@ -638,6 +677,8 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, dist)
+        elif args.profile:
+            profile_case(args, dist)
         elif args.workload == "uniform":
             gpu_arm(args, dist)
         else:

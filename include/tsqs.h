@@ -63,9 +63,9 @@ typedef enum {
 typedef struct {
     int32_t  tile_items;       /* partition kernel shape, 0..3 (0 = default), given as
                                   consumer threads x keys per thread x staged tiles:
-                                  4-byte keys 256x32x3, 256x16x3, 512x16x2, 128x16x4;
-                                  8-byte keys 256x8x3, 256x8x4, 512x8x2, 128x8x4;
-                                  records     256x4x3, 256x4x4, 512x4x2, 128x4x4     */
+                                  4-byte keys 192x32x3, 256x24x3, 256x32x3, 256x16x3;
+                                  8-byte keys 192x16x3, 256x12x3, 256x16x3, 256x8x3;
+                                  records     192x8x3,  256x6x3,  256x8x3,  256x4x3      */
     int32_t  small_threshold;  /* segments of <= this many elements finish on chip, 512..4096;
                                   capped per kind at 4096 (4-byte), 2048 (8-byte), 1024
                                   (records): the largest leaf one warp holds in registers */

@@ -26,10 +26,10 @@ KindOps make_ops() {
     o.pivot_block = kPivotBlock;
     o.leaf_smem = (int)LeafLayout<KIND>::bytes;
     o.leaf_max = kMaxSmall;
-    o.part[0] = part_variant<KIND, 256, 4, 3>();
-    o.part[1] = part_variant<KIND, 256, 4, 4>();
-    o.part[2] = part_variant<KIND, 512, 4, 2>();
-    o.part[3] = part_variant<KIND, 128, 4, 4>();
+    o.part[0] = part_variant<KIND, 192, 8, 3>();
+    o.part[1] = part_variant<KIND, 256, 6, 3>();
+    o.part[2] = part_variant<KIND, 256, 8, 3>();
+    o.part[3] = part_variant<KIND, 256, 4, 3>();
     o.k_init = (const void *)k_init<KIND>;
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 1>;
     o.k_pivot = (const void *)k_pivot<KIND>;

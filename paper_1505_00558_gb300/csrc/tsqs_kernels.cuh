@@ -568,13 +568,21 @@ struct PartLayout {
     static_assert(2 * 24 <= 128, "misc area");
 };
 
+// Resident CTAs per SM the register budget of a partition shape aims at; `words` is
+// the 32-bit registers one thread's keys take (keys per thread x key size / 4).
+constexpr int part_min_blocks(int block, int words) {
+    return words >= 32 ? (block >= 256 ? 2 : (block >= 192 ? 3 : 4))
+         : words >= 24 ? 3
+         : (block >= 512 ? 2 : (block >= 256 ? 4 : 6));
+}
+
 struct PartMisc {
     unsigned long long ex_lt, ex_gt;
     uint32_t total, pad;
 };
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
-__global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 : 4) : (BLOCK >= 512 ? 2 : (BLOCK >= 256 ? 4 : 6)))) k_partition(const Job *__restrict__ job, Ctl *ctl) {
+__global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (int)sizeof(typename Key<KIND>::S) / 4)) k_partition(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
@@ -785,7 +793,8 @@ __global__ void __launch_bounds__(BLOCK + 32, (ITEMS >= 32 ? (BLOCK >= 256 ? 2 :
                 // all of this thread's keys go to one run (ordered input): write them
                 // permuted by the lane inside the thread's own stretch of the run, so
                 // that a warp's store covers 32 banks instead of one
-                const uint32_t rot = (lane & (uint32_t)(ITEMS - 1)) * es;
+                constexpr uint32_t kRot = (uint32_t)(ITEMS & -ITEMS) - 1u;   // keeps k ^ rot < ITEMS
+                const uint32_t rot = (lane & kRot) * es;
                 const uint32_t base = ltm == kAll ? la : ga;
                 const int sgn = ltm == kAll ? 1 : -1;
 #pragma unroll
