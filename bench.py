@@ -601,24 +601,29 @@ def _gen_request(torch, kind_rec, n, pattern, seed, dev):
 
 
 def serving_workload(args, dist, torch, T):
-    """Poisson stream of sort requests, sizes floor(2^(10 + 14U)), 70% int32 / 30%
-    (u64, u64) records, patterns from the seven, admitted under a 40 GB budget.
-    The offered load is 0.7 x the sustained throughput measured with every request
-    submitted at once."""
+    """Poisson stream of 50,000 sort requests, sizes floor(2^(10 + 14U)), 70% int32 /
+    30% (u64, u64) records, patterns from the seven, admitted under a 40 GB budget.
+    The offered load is 0.7 x the sustained throughput measured with the requests
+    submitted as fast as buffers free up.  Request contents come from a pool of 2,000
+    distinct generated requests: request i sorts a fresh copy of pool entry i mod 2000
+    (its buffer is restored once request i - 2000 on it has finished); the arrival
+    gaps are drawn for all 50,000."""
     from workloads import PATTERNS
     from workloads.patterns import serving_requests
-    nreq = int(os.environ.get("TSQS_SERVE_REQUESTS", "2000"))
+    nreq = int(os.environ.get("TSQS_SERVE_REQUESTS", "50000"))
+    npool = min(nreq, int(os.environ.get("TSQS_SERVE_POOL", "2000")))
     req = serving_requests(nreq, seed=1)
     dev = torch.device("cuda")
-    bufs, pristine = [], []
-    for i in range(nreq):
-        t = _gen_request(torch, bool(req["is_rec"][i]), int(req["sizes"][i]),
-                         PATTERNS[int(req["pattern"][i])], i, dev)
-        pristine.append(t)
+    pristine = []
+    for j in range(npool):
+        pristine.append(_gen_request(torch, bool(req["is_rec"][j]), int(req["sizes"][j]),
+                                     PATTERNS[int(req["pattern"][j])], j, dev))
     torch.cuda.synchronize()
-    keys = [int(x) for x in req["sizes"]]
-    total_keys = sum(keys)
+    sizes = [int(req["sizes"][i % npool]) for i in range(nreq)]
+    is_rec = [bool(req["is_rec"][i % npool]) for i in range(nreq)]
+    total_keys = sum(sizes)
     lib = T.lib()
+    stream = torch.cuda.current_stream()
 
     def run(lam):
         work = [p.clone() for p in pristine]
@@ -627,14 +632,25 @@ def serving_workload(args, dist, torch, T):
         assert srv
         arrive = np.cumsum(req["gaps"] / lam) if lam else np.zeros(nreq)
         tickets = [None] * nreq
+        r = T.Result()
+        held = 0                       # polls that found an arrival's pool buffer still busy
         t0 = time.perf_counter()
         i = 0
         while True:
             now = time.perf_counter() - t0
             while i < nreq and arrive[i] <= now:
+                j = i % npool
+                if i >= npool:
+                    # the buffer's previous request must be finished before its reuse
+                    lib.tsqs_server_poll(srv, tickets[i - npool], ctypes.byref(r))
+                    if not r.done:
+                        held += 1
+                        break
+                    work[j].copy_(pristine[j])
+                    stream.synchronize()
                 tk = ctypes.c_uint64()
-                kind, es = (T.TSQS_U64_U64_REC, 16) if req["is_rec"][i] else (T.TSQS_I32, 4)
-                rc = lib.tsqs_server_submit(srv, ctypes.c_void_p(work[i].data_ptr()), keys[i], es,
+                kind, es = (T.TSQS_U64_U64_REC, 16) if is_rec[i] else (T.TSQS_I32, 4)
+                rc = lib.tsqs_server_submit(srv, ctypes.c_void_p(work[j].data_ptr()), sizes[i], es,
                                             kind, ctypes.byref(tk))
                 assert rc == 0, rc
                 tickets[i] = tk.value
@@ -644,9 +660,9 @@ def serving_workload(args, dist, torch, T):
                 break
         res = []
         for k in range(nreq):
-            r = T.Result()
-            lib.tsqs_server_poll(srv, tickets[k], ctypes.byref(r))
-            res.append((r.t_submit, r.t_start, r.t_done, r.status, r.batch_size, r.batch_id))
+            rr = T.Result()
+            lib.tsqs_server_poll(srv, tickets[k], ctypes.byref(rr))
+            res.append((rr.t_submit, rr.t_start, rr.t_done, rr.status, rr.batch_size, rr.batch_id))
         lib.tsqs_server_destroy(srv)
         t_sub = np.array([x[0] for x in res])
         t_done = np.array([x[2] for x in res])
@@ -658,16 +674,18 @@ def serving_workload(args, dist, torch, T):
                 "mean_ms": float(lat.mean()), "sustained_mkeys_s": total_keys / span / 1e6,
                 "span_s": span, "status_ok": ok, "spot_sorted": sorted_ok,
                 "batches": len(set(x[5] for x in res)),
-                "mean_batch": float(np.mean([x[4] for x in res]))}
+                "mean_batch": float(np.mean([x[4] for x in res])),
+                "pool_busy_polls": held}
 
     run(None)                                             # warm graphs and lanes
     sat = run(None)
     lam = 0.7 * sat["sustained_mkeys_s"] * 1e6 / (total_keys / nreq)
     load = run(lam)
     _line(args, dist, load["sustained_mkeys_s"],
-          {"workload": f"serving: {nreq} Poisson requests, sizes 2^10..2^24 log-uniform, 70% int32 / "
-                       "30% u64+u64 records, seven patterns, 40 GB budget, 4 lanes",
-           "requests": nreq, "offered_load_req_s": lam},
+          {"workload": f"serving: {nreq} Poisson requests (contents from a pool of {npool}), "
+                       "sizes 2^10..2^24 log-uniform, 70% int32 / 30% u64+u64 records, seven "
+                       "patterns, 40 GB budget, 4 lanes",
+           "requests": nreq, "pool": npool, "offered_load_req_s": lam},
           {"at_offered_load": load, "saturated": sat}, ms=load["mean_ms"])
 
 

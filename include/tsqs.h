@@ -66,9 +66,8 @@ typedef struct {
                                   4-byte keys 192x32x3, 256x24x3, 256x32x3, 256x16x3;
                                   8-byte keys 192x16x3, 256x12x3, 256x16x3, 256x8x3;
                                   records     192x8x3,  256x6x3,  256x8x3,  256x4x3      */
-    int32_t  small_threshold;  /* segments of <= this many elements finish on chip, 512..4096;
-                                  capped per kind at 4096 (4-byte), 2048 (8-byte), 1024
-                                  (records): the largest leaf one warp holds in registers */
+    int32_t  small_threshold;  /* segments of <= this many elements finish on chip,
+                                  512..4096 (default 4096) for every key kind          */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */
     int32_t  sample_count;     /* pivot sample size (odd, at most 63; default 31)       */
     int32_t  offset_mode;      /* where a tile writes its <p and >p runs:
