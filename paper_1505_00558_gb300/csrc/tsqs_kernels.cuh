@@ -676,6 +676,9 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
     }
 
     // ================================ consumers ================================
+    // job fields read once: the asm memory clobbers below would otherwise reload them
+    const uint32_t c_offset_mode = job->offset_mode, c_vec_off = job->vec_off;
+    unsigned long long *const c_cursor = job->seg_cursor;
     // Two-stage software pipeline over this CTA's tiles: phase A of tile i (classify,
     // scan, stage in place, reserve the output runs) runs before phase B of tile i-1
     // (write-out), so the reservation's round trip overlaps with the next tile's work.
@@ -779,8 +782,8 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
             // atomic mode: one 64-bit atomic on the segment's cursor reserves both runs
             // (#<p in the low word, #>p in the high word); its result is used one tile
             // later
-            if (tid == 0 && job->offset_mode == 0u)
-                resv = atomicAdd(job->seg_cursor + m.si, (unsigned long long)((agg_gt << 32) | agg_lt));
+            if (tid == 0 && c_offset_mode == 0u)
+                resv = atomicAdd(c_cursor + m.si, (unsigned long long)((agg_gt << 32) | agg_lt));
             // stage without branches: <p from the front, >p from the back, =p (and
             // elements outside the segment) into the dummy slot at TILE
             // (32-bit shared-window addresses keep the address arithmetic to one add)
@@ -809,7 +812,7 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
                     ga -= g ? es : 0u;
                 }
             }
-            if (warp == 0 && job->offset_mode != 0u) {
+            if (warp == 0 && c_offset_mode != 0u) {
                 // look-back mode: publish the aggregate, walk back, publish the inclusive
                 uint64_t ex_lt = 0, ex_gt = 0;
                 unsigned long long *stw = job->tile_status + m.tile;
@@ -833,8 +836,8 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
             const uint32_t tlt = pm.total & 0xFFFFu, tgt = pm.total >> 16;
             // <p run: staged [0, tlt) -> dst[sb + ex_lt, +tlt); >p run: staged
             // [TILE - tgt, TILE) -> dst[se - ex_gt - tgt, se - ex_gt), both ascending
-            copy_run<S, V, BLOCK>(dst, prev_sb + pm.ex_lt, pbuf, tlt, job->vec_off);
-            copy_run<S, V, BLOCK>(dst, prev_se - pm.ex_gt - tgt, pbuf + (TILE - tgt), tgt, job->vec_off);
+            copy_run<S, V, BLOCK>(dst, prev_sb + pm.ex_lt, pbuf, tlt, c_vec_off);
+            copy_run<S, V, BLOCK>(dst, prev_se - pm.ex_gt - tgt, pbuf + (TILE - tgt), tgt, c_vec_off);
         }
         fence_proxy_async();
         consumer_sync<BLOCK>();        // previous buffer fully read, this tile staged
