@@ -19,6 +19,7 @@ namespace tsqs {
 
 constexpr int kMaxSamples = 63;
 constexpr uint32_t kFillChunk = 16384;      // =p fills are split into items of this size
+constexpr uint32_t kInlineFill = 16;        // =p runs up to this long are written by the level-end kernel
 constexpr int kMaxSmall = 4096;             // largest on-chip segment
 constexpr int kStatLevels = 64;
 

@@ -1320,7 +1320,17 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
                 nlf++;
             }
         }
-        const uint32_t nch = (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
+        // a short =p run is written right here (no later kernel reads or writes it), so
+        // the leaf pass does not spend a claim round trip on a one-element fill
+        const bool inline_fill = eqe - eqb <= kInlineFill;
+        const uint32_t nch = inline_fill ? 0u : (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
+        uint64_t ifill = 0;
+        if (inline_fill && eqe > eqb) {
+            typename K::S *outp = reinterpret_cast<typename K::S *>(job->base);
+            const typename K::S val = K::uncanon(c_from<typename K::C>(piv_lo, piv_hi));
+            for (uint64_t x = eqb; x < eqe; x++) outp[x] = val;
+            ifill = eqe - eqb;
+        }
         nlf += nch;
         // warp-exclusive offsets and one atomic per counter
         uint32_t xf = nfr, xt = ntl, xl = nlf;
@@ -1331,15 +1341,19 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
             const uint32_t c2 = __shfl_up_sync(0xffffffffu, xl, o);
             if (lane >= (uint32_t)o) { xf += a; xt += b2; xl += c2; }
         }
-        uint64_t ksum = keys;
+        uint64_t ksum = keys, fsum = ifill;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ksum += __shfl_xor_sync(0xffffffffu, ksum, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            ksum += __shfl_xor_sync(0xffffffffu, ksum, o);
+            fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+        }
         uint32_t bf = 0, bt = 0, bl = 0;
         if (lane == 31) {
             bf = atomicAdd(&ctl->nfront[np], xf);
             bt = atomicAdd(&ctl->ntiles[np], xt);
             bl = atomicAdd(&ctl->nleaf, xl);
             if (ksum) atomicAdd((unsigned long long *)&ctl->front_keys[np], (unsigned long long)ksum);
+            if (fsum) atomicAdd((unsigned long long *)&ctl->leaf_filled, (unsigned long long)fsum);
         }
         bf = __shfl_sync(0xffffffffu, bf, 31) + xf - nfr;
         bt = __shfl_sync(0xffffffffu, bt, 31) + xt - ntl;
