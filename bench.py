@@ -400,7 +400,8 @@ def gpu_arm(args, dist):
         tt = dist.max(sum(times))
         e2e = {"value": dist.sum(float(len(times) * n)) / tt / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4,
-               "api": "tsqs_sort_host (pinned host array in, sorted host array out)",
+               "api": "tsqs_sort_host: pinned host array in (copy engine), sorted result "
+                      "written into it by the kernels over the host link",
                "sorted": e2e_ok}
 
     cpu = None

@@ -112,8 +112,11 @@ int tsqs_sort_segmented(void *base, size_t nmemb_total, const uint64_t *d_seg_of
                         size_t nseg, size_t elem_size, int key_kind, void *stream);
 
 /* Host-memory convenience (the paper's qsort(): array in host memory).  Copies h_base
- * to library-owned device memory, sorts, copies back, and synchronises `stream`
- * before returning.  h_base should be pinned for full copy bandwidth. */
+ * to library-owned device memory and sorts it there.  If h_base is page-locked and
+ * mapped (cudaHostAlloc / cudaHostRegister / a pinned torch tensor), the kernels write
+ * the sorted result straight into h_base, so the last on-chip pass overlaps the
+ * transfer back; any other host array is copied back after the sort.  Synchronises
+ * `stream` before returning. */
 int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
 
 /* Frees the default context's device scratch (Section III.G:

@@ -224,6 +224,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     memset(j, 0, sizeof(*j));
     const uintptr_t b = (uintptr_t)base;
     j->base = base;
+    j->out = base;
     j->alt = c->scratch + L.alt_off + (b & 15u);
     j->n = n;
     j->seg_offsets = offs;
@@ -343,7 +344,7 @@ int validate(void *base, size_t nmemb, size_t elem_size, int key_kind) {
 
 // Queues one sort (single segment when offs == nullptr).
 int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t nseg,
-               size_t elem_size, int key_kind, cudaStream_t stream) {
+               size_t elem_size, int key_kind, cudaStream_t stream, void *out = nullptr) {
     int rc = validate(base, n, elem_size, key_kind);
     if (rc) return rc;
     if (!offs && n >= (1ull << 31)) return TSQS_EINVAL;
@@ -358,6 +359,7 @@ int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t n
     if ((rc = ctx_build_graph(c, o))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, n, offs, nseg, &j))) return rc;
+    if (out) j.out = out;
     if (c->ev_valid) CK(cudaStreamWaitEvent(stream, c->done_ev, 0));
     k_setup<<<1, 256, 0, stream>>>(c->d_job, c->d_ctl, j);
     CK(cudaGetLastError());
@@ -567,15 +569,34 @@ int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, v
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_host_mu);
     const size_t bytes = nmemb * elem_size;
-    if (bytes > g_host_dev_bytes) {
+    // device copy of the input, allocated with 16 bytes of slack so that it can take the
+    // host array's 16-byte phase (the vector stores of the output then line up on both)
+    if (bytes + 16 > g_host_dev_bytes) {
         if (g_host_dev) { CK(cudaStreamSynchronize(s)); cudaFree(g_host_dev); g_host_dev = nullptr; g_host_dev_bytes = 0; }
-        if (cudaMalloc(&g_host_dev, bytes) != cudaSuccess) { cudaGetLastError(); return TSQS_ENOMEM; }
-        g_host_dev_bytes = bytes;
+        if (cudaMalloc(&g_host_dev, bytes + 16) != cudaSuccess) { cudaGetLastError(); return TSQS_ENOMEM; }
+        g_host_dev_bytes = bytes + 16;
     }
-    CK(cudaMemcpyAsync(g_host_dev, h_base, bytes, cudaMemcpyHostToDevice, s));
-    rc = tsqs_sort(g_host_dev, nmemb, elem_size, key_kind, stream);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(h_base, g_host_dev, bytes, cudaMemcpyDeviceToHost, s));
+    char *dev = (char *)g_host_dev + ((uintptr_t)h_base & 15u);
+    // a pinned (page-locked, device-mapped) host array receives the result straight from
+    // the kernels over the host link, so the final leaf pass overlaps the transfer back;
+    // any other host array gets a copy after the sort
+    void *h_mapped = nullptr;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, h_base) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer && (((uintptr_t)pa.devicePointer ^ (uintptr_t)h_base) & 15u) == 0)
+        h_mapped = pa.devicePointer;
+    cudaGetLastError();
+    CK(cudaMemcpyAsync(dev, h_base, bytes, cudaMemcpyHostToDevice, s));
+    if (h_mapped) {
+        tsqs_ctx *c = default_ctx();
+        if (!c) return TSQS_ENOMEM;
+        rc = ctx_launch(c, dev, nmemb, nullptr, 0, elem_size, key_kind, s, h_mapped);
+        if (rc) return rc;
+    } else {
+        rc = tsqs_sort(dev, nmemb, elem_size, key_kind, stream);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h_base, dev, bytes, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     return TSQS_OK;
 }
@@ -797,6 +818,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     memset(j, 0, sizeof(*j));
     const uintptr_t b = (uintptr_t)base;
     j->base = base;
+    j->out = base;
     j->alt = scratch + L.alt_off + (b & 15u);
     j->n = n;
     j->seg_offsets = nullptr;

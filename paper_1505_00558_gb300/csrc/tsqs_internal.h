@@ -69,6 +69,8 @@ struct Ctl {
 struct Job {
     void *base;               // buffer 0: the caller's array
     void *alt;                // buffer 1: scratch with the same 16-byte phase as base
+    void *out;                // where leaf sorts and =p fills write the result: base, or a
+                              // device-mapped host array with base's 16-byte phase
     uint64_t n;               // elements addressable in base (and alt)
     const uint64_t *seg_offsets;   // nullptr: one segment [0, n)
     uint64_t nseg;

@@ -1076,7 +1076,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     // change while this kernel runs, so every block takes the same decision.
     const uint32_t nl = min(ctl->nleaf, job->cap_leaves);
     if (!final_pass && nl <= job->leaf_defer) return;
-    S *out = reinterpret_cast<S *>(job->base);
+    S *out = reinterpret_cast<S *>(job->out);
     const int64_t n = (int64_t)job->n;
     const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
     const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
@@ -1326,7 +1326,7 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
         const uint32_t nch = inline_fill ? 0u : (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
         uint64_t ifill = 0;
         if (inline_fill && eqe > eqb) {
-            typename K::S *outp = reinterpret_cast<typename K::S *>(job->base);
+            typename K::S *outp = reinterpret_cast<typename K::S *>(job->out);
             const typename K::S val = K::uncanon(c_from<typename K::C>(piv_lo, piv_hi));
             for (uint64_t x = eqb; x < eqe; x++) outp[x] = val;
             ifill = eqe - eqb;

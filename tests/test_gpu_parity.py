@@ -337,3 +337,40 @@ def test_offset_modes_match_oracle(T, orc, offset_mode):
         assert ctx.status() == 0
         assert from_dev(t, np.int32).tobytes() == oracle_sort(orc, a, 1).tobytes()
     ctx.close()
+
+
+# ------------------------------------------------------------------------------
+# host-memory entry point: pinned arrays get the result straight from the kernels,
+# pageable ones a copy after the sort; both at every 16-byte phase
+# ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("off", [0, 1, 3])
+def test_host_sort_int32_matches_oracle(T, orc, pinned, off):
+    n = 300_007
+    a = int32_pattern("random", n + off + 2, seed=21 + off)
+    exp = oracle_sort(orc, a[off:off + n], 1)
+    h = torch.from_numpy(a.copy())
+    if pinned:
+        h = h.pin_memory()
+    view = h[off:off + n]
+    rc = T.lib().tsqs_sort_host(ctypes.c_void_p(view.data_ptr()), n, 4, 1, None)
+    assert rc == 0
+    got = h.numpy()
+    assert got[off:off + n].tobytes() == exp.tobytes()
+    assert got[:off].tobytes() == a[:off].tobytes()               # neighbours untouched
+    assert got[off + n:].tobytes() == a[off + n:].tobytes()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_sort_records_matches_oracle(T, orc, pinned):
+    n = 70_001
+    r = records_u64(n, seed=33)
+    exp = r.copy()
+    orc.tsqs_sort(exp, 7)
+    h = torch.from_numpy(r.view(np.int64).copy())
+    if pinned:
+        h = h.pin_memory()
+    rc = T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, 16, 7, None)
+    assert rc == 0
+    assert h.numpy().view(np.uint64).reshape(n, 2).tobytes() == exp.tobytes()
