@@ -5,6 +5,9 @@
  * The library replaces qsort() for fixed key kinds (the paper's stated goal, abstract
  * and Section VII): a comparator pointer becomes a key kind, the element size must
  * match that kind, and the sort runs on one CUDA device (sm_103a) as
+ *   presortedness     a root segment whose sample is in order is checked in full and,
+ *                     if it is non-decreasing (non-increasing), finished as it stands
+ *                     (by one reversal)                          (Section III.I)
  *   pivot kernel      a sampled median per segment        (Section III.H, V.C)
  *   partition kernel  <p | =p | >p split of every segment (Section III.A-F)
  *   work queue        device-built segment frontier that replaces recursion (Fig. 1)
@@ -87,6 +90,8 @@ typedef struct {
     uint64_t leaf_sorted_keys; /* keys finished by the on-chip sorter                   */
     uint64_t leaf_filled_keys; /* keys written by =p fills                              */
     uint64_t leaf_items;       /* leaf work items processed                             */
+    uint64_t presorted_keys;   /* keys of root segments found already in order or in
+                                  reverse order (finished without a partition level)   */
     uint32_t level_keys_count; /* entries used in level_keys                            */
     uint32_t pad;
     uint64_t level_keys[64];   /* keys partitioned at level i (first 64 levels)         */

@@ -34,6 +34,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_uint32), ("max_frontier", ctypes.c_uint32),
                 ("partition_keys", ctypes.c_uint64), ("leaf_sorted_keys", ctypes.c_uint64),
                 ("leaf_filled_keys", ctypes.c_uint64), ("leaf_items", ctypes.c_uint64),
+                ("presorted_keys", ctypes.c_uint64),
                 ("level_keys_count", ctypes.c_uint32), ("pad", ctypes.c_uint32),
                 ("level_keys", ctypes.c_uint64 * 64)]
 

@@ -53,7 +53,7 @@ size_t kind_size(int kind) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, misc_off, total;
+    size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, presort_off, misc_off, total;
     uint32_t cap_front, cap_tiles, cap_leaves, leaf_defer;
 };
 
@@ -89,6 +89,7 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     L.tstat_off = off;          off = align_up(off + ct * sizeof(unsigned long long), 256);
     L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
     L.cursor_off = off;         off = align_up(off + cf * sizeof(unsigned long long), 256);
+    L.presort_off = off;        off = align_up(off + (nseg ? nseg : 1) * sizeof(uint32_t), 256);
     L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
     L.total = off;
     return L;
@@ -236,6 +237,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->tile_status = (unsigned long long *)(c->scratch + L.tstat_off);
     j->seg_done = (uint32_t *)(c->scratch + L.done_off);
     j->seg_cursor = (unsigned long long *)(c->scratch + L.cursor_off);
+    j->presort = (uint32_t *)(c->scratch + L.presort_off);
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
@@ -264,13 +266,22 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
 
+    // presortedness: sample orientation, full check of the candidates, finish them
     cudaKernelNodeParams kp{};
-    kp.func = (void *)o->k_init;
-    kp.gridDim = dim3(c->sms * 2);
+    cudaGraphNode_t n_ori, n_chk, n_pre, n_init;
+    kp.func = (void *)o->k_orient;
+    kp.gridDim = dim3(c->sms * 4);
     kp.blockDim = dim3(256);
     kp.kernelParams = args2;
-    cudaGraphNode_t n_init;
-    CK(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp));
+    CK(cudaGraphAddKernelNode(&n_ori, g, nullptr, 0, &kp));
+    kp.func = (void *)o->k_check;
+    kp.gridDim = dim3(c->sms * 4);
+    CK(cudaGraphAddKernelNode(&n_chk, g, &n_ori, 1, &kp));
+    kp.func = (void *)o->k_presort;
+    CK(cudaGraphAddKernelNode(&n_pre, g, &n_chk, 1, &kp));
+    kp.func = (void *)o->k_init;
+    kp.gridDim = dim3(c->sms * 2);
+    CK(cudaGraphAddKernelNode(&n_init, g, &n_pre, 1, &kp));
 
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
@@ -506,6 +517,7 @@ int tsqs_ctx_stats(tsqs_ctx *c, void *stream, tsqs_stats *out) {
     out->leaf_sorted_keys = h.leaf_sorted;
     out->leaf_filled_keys = h.leaf_filled;
     out->leaf_items = h.leaf_items;
+    out->presorted_keys = h.presorted;
     const uint32_t nl = std::min<uint32_t>(h.level, (uint32_t)kStatLevels);
     out->level_keys_count = nl;
     for (uint32_t i = 0; i < nl; i++) out->level_keys[i] = h.level_keys[i];
@@ -637,6 +649,9 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     cudaEvent_t ev[4];
     for (auto &e : ev) CK(cudaEventCreate(&e));
     k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
+    CK(cudaLaunchKernel(o->k_orient, dim3(c->sms * 4), dim3(256), args2, 0, s));
+    CK(cudaLaunchKernel(o->k_check, dim3(c->sms * 4), dim3(256), args2, 0, s));
+    CK(cudaLaunchKernel(o->k_presort, dim3(c->sms * 4), dim3(256), args2, 0, s));
     CK(cudaLaunchKernel(o->k_init, dim3(c->sms * 2), dim3(256), args2, 0, s));
     int L = 0;
     for (;;) {
@@ -830,6 +845,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     j->tile_status = (unsigned long long *)(scratch + L.tstat_off);
     j->seg_done = (uint32_t *)(scratch + L.done_off);
     j->seg_cursor = (unsigned long long *)(scratch + L.cursor_off);
+    j->presort = (uint32_t *)(scratch + L.presort_off);
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;

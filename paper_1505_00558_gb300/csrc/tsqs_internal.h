@@ -55,6 +55,7 @@ struct Ctl {
     uint32_t ntiles[2];
     uint32_t nleaf;           // leaf items queued (across levels, until a leaf pass)
     uint32_t leaf_blocks;     // leaf-pass blocks finished (last one empties the queue)
+    uint32_t presort_any;     // some root segment's sample is in order (presortedness pass)
     uint32_t max_front;
     uint32_t levels_done;
     uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
@@ -62,6 +63,7 @@ struct Ctl {
     uint64_t front_keys[2];
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;
+    uint64_t presorted;       // keys of root segments found already in order (or reversed)
     uint64_t level_keys[kStatLevels];
 };
 
@@ -80,6 +82,8 @@ struct Job {
     unsigned long long *tile_status;   // decoupled look-back words, current level
     uint32_t *seg_done;       // finished tiles per frontier segment
     unsigned long long *seg_cursor;    // reserved (#<p | #>p << 32) per frontier segment
+    uint32_t *presort;        // per root segment: 0, or 1 / 2 while it may be / is known to be
+                              // non-decreasing / non-increasing
     uint32_t cap_front, cap_tiles, cap_leaves;
     uint32_t leaf_defer;      // a level's leaf pass runs only above this many queued items
     uint32_t small_T;         // on-chip threshold
@@ -119,6 +123,7 @@ struct KindOps {
     int leaf_max;             // largest segment the leaf kernel sorts (32 x keys per lane)
     PartVariant part[kPartVariants];   // [0] is the default shape
     const void *k_init, *k_leaf, *k_pivot, *k_finish;
+    const void *k_orient, *k_check, *k_presort;
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
 };
 

@@ -31,6 +31,9 @@ KindOps make_ops() {
     o.part[2] = part_variant<KIND, 256, 32, 3>();
     o.part[3] = part_variant<KIND, 256, 16, 3>();
     o.k_init = (const void *)k_init<KIND>;
+    o.k_orient = (const void *)k_orient<KIND>;
+    o.k_check = (const void *)k_check<KIND>;
+    o.k_presort = (const void *)k_presort<KIND>;
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 4>;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;

@@ -326,7 +326,145 @@ __global__ void k_init(const Job *__restrict__ job, Ctl *ctl) {
         const uint64_t e = job->seg_offsets ? job->seg_offsets[s + 1] : job->n;
         if (e < b || e > job->n || e - b >= (1ull << 31)) { set_status(ctl, TSQS_EINVAL); continue; }
         if (e - b <= 1) continue;
+        if (job->presort[s] != 0u) continue;             // already in order (presortedness pass)
         push_segment<K::V>(job, ctl, 0, b, e);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Presortedness (the GPU counterpart of Section III.I's possibly-sorted and possibly-
+// reversed handlers).  The paper reads the orientation of its median-of-3 sample and,
+// when the sample is in order, checks the segment while partitioning.  Here every root
+// segment above the on-chip threshold draws 31 evenly spaced samples (one warp); a
+// segment whose samples are non-decreasing (or non-increasing) is checked in full by a
+// chunked pass that stops early once an adjacent pair is out of order.  A segment that
+// passes is final as it stands (non-decreasing) or after one reversal (non-increasing),
+// and k_init leaves it out of the level loop.  Random input pays one warp of samples
+// per root segment and two launches that return at once.
+// ---------------------------------------------------------------------------------
+
+constexpr int kPresortChunk = 8192;
+
+__device__ __forceinline__ void root_bounds(const Job *job, uint64_t s, uint64_t &b, uint64_t &e) {
+    b = job->seg_offsets ? job->seg_offsets[s] : 0;
+    e = job->seg_offsets ? job->seg_offsets[s + 1] : job->n;
+}
+
+// Root segment containing element x (the last s with offsets[s] <= x), by binary search.
+__device__ __forceinline__ uint64_t root_of(const Job *job, uint64_t x) {
+    if (!job->seg_offsets) return 0;
+    uint64_t lo = 0, hi = job->nseg;                  // offsets[lo] <= x < offsets[hi]
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (job->seg_offsets[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int KIND>
+__global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
+    using K = Key<KIND>;
+    using C = typename K::C;
+    const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const typename K::S *src = buffer<K>(job, 0);
+    for (uint64_t s = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
+        uint64_t b, e;
+        root_bounds(job, s, b, e);
+        uint32_t flag = 0;
+        if (e > b && e <= job->n && e - b > (uint64_t)job->small_T) {
+            const uint64_t m = e - b;
+            const uint32_t k = min(lane, 30u);          // 31 samples, first and last included
+            const C x = K::canon(src[b + ((m - 1) * k) / 30u]);
+            const C y = c_shfl(x, (int)((lane + 1u) & 31u));   // lanes 30, 31 compare nothing
+            const bool up_ok = lane >= 30u || !c_lt(y, x);
+            const bool down_ok = lane >= 30u || !c_lt(x, y);
+            if (__all_sync(0xffffffffu, up_ok)) flag = 1;
+            else if (__all_sync(0xffffffffu, down_ok)) flag = 2;
+        }
+        if (lane == 0) {
+            job->presort[s] = flag;
+            if (flag) atomicOr(&ctl->presort_any, 1u);
+        }
+    }
+}
+
+// Clears the flag of every candidate segment that has an adjacent pair out of order.
+template <int KIND>
+__global__ void k_check(const Job *__restrict__ job, Ctl *ctl) {
+    using K = Key<KIND>;
+    if (*(volatile const uint32_t *)&ctl->presort_any == 0u) return;
+    const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
+    const uint64_t n = job->n;
+    const typename K::S *src = buffer<K>(job, 0);
+    __shared__ uint64_t s_first;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kPresortChunk; c0 < n; c0 += (uint64_t)gridDim.x * kPresortChunk) {
+        const uint64_t c1 = min(c0 + (uint64_t)kPresortChunk, n);
+        if (threadIdx.x == 0) s_first = root_of(job, c0);
+        __syncthreads();
+        for (uint64_t s = s_first; s < nseg; s++) {
+            uint64_t b, e;
+            root_bounds(job, s, b, e);
+            if (b >= c1) break;
+            const uint32_t flag = *(volatile const uint32_t *)&job->presort[s];
+            if (flag == 0u || e <= c0 || e <= b) continue;
+            // pairs (i, i + 1) with i in [max(c0, b), min(c1, e - 1))
+            const uint64_t i0 = max(c0, b), i1 = min(c1, e - 1);
+            bool bad = false;
+            for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const typename K::C x = K::canon(src[i]), y = K::canon(src[i + 1]);
+                bad |= flag == 1u ? c_lt(y, x) : c_lt(x, y);
+            }
+            if (__syncthreads_or(bad) && threadIdx.x == 0) job->presort[s] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// Finishes every segment that passed: reverses a non-increasing one, and writes either
+// kind to the output array when that is not the input array.
+template <int KIND>
+__global__ void k_presort(const Job *__restrict__ job, Ctl *ctl) {
+    using K = Key<KIND>;
+    using S = typename K::S;
+    if (*(volatile const uint32_t *)&ctl->presort_any == 0u) return;
+    const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
+    const uint64_t n = job->n;
+    S *src = buffer<K>(job, 0);
+    S *out = reinterpret_cast<S *>(job->out);
+    const bool in_place = job->out == job->base;
+    __shared__ uint64_t s_first;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kPresortChunk; c0 < n; c0 += (uint64_t)gridDim.x * kPresortChunk) {
+        const uint64_t c1 = min(c0 + (uint64_t)kPresortChunk, n);
+        if (threadIdx.x == 0) s_first = root_of(job, c0);
+        __syncthreads();
+        for (uint64_t s = s_first; s < nseg; s++) {
+            uint64_t b, e;
+            root_bounds(job, s, b, e);
+            if (b >= c1) break;
+            const uint32_t flag = job->presort[s];
+            if (flag == 0u || e <= b) continue;
+            if (threadIdx.x == 0 && c0 <= b && b < c1)
+                atomicAdd((unsigned long long *)&ctl->presorted, (unsigned long long)(e - b));
+            if (flag == 1u) {
+                if (!in_place)
+                    for (uint64_t i = max(c0, b) + threadIdx.x; i < min(c1, e); i += blockDim.x) out[i] = src[i];
+            } else if (in_place) {
+                // swap i with its mirror for every i of the first half that lies in the chunk
+                const uint64_t h = b + (e - b) / 2;
+                for (uint64_t i = max(c0, b) + threadIdx.x; i < min(c1, h); i += blockDim.x) {
+                    const uint64_t j = e - 1 - (i - b);
+                    const S t = src[i];
+                    src[i] = src[j];
+                    src[j] = t;
+                }
+            } else {
+                for (uint64_t i = max(c0, b) + threadIdx.x; i < min(c1, e); i += blockDim.x)
+                    out[e - 1 - (i - b)] = src[i];
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -127,7 +127,11 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
     // arrays is read before it is rewritten
     k_setup<<<1, 256, 0, s>>>(d.job, d.ctl, j);
     if (cudaGetLastError() != cudaSuccess) return TSQS_ECUDA;
-    if (cudaLaunchKernel(o->k_init, dim3(d.sms * 2), dim3(256), args2, 0, s) != cudaSuccess) return TSQS_ECUDA;
+    if (cudaLaunchKernel(o->k_orient, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
+        cudaLaunchKernel(o->k_check, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
+        cudaLaunchKernel(o->k_presort, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
+        cudaLaunchKernel(o->k_init, dim3(d.sms * 2), dim3(256), args2, 0, s) != cudaSuccess)
+        return TSQS_ECUDA;
     for (uint32_t level = 0; level <= j.max_levels; level++) {
         if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl,
                              (size_t)o->leaf_smem, s) != cudaSuccess ||

@@ -316,7 +316,7 @@ def test_context_stats(T):
     T.sort_(t, kind=1, ctx=ctx)
     st = ctx.stats()
     assert ctx.status() == 0
-    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] == len(a)
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] + st["presorted_keys"] == len(a)
     assert st["levels"] >= 10 and st["level_keys"][0] == len(a)
     assert np.array_equal(t.cpu().numpy(), np.sort(a))
     ctx.close()
@@ -374,3 +374,112 @@ def test_host_sort_records_matches_oracle(T, orc, pinned):
     rc = T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, 16, 7, None)
     assert rc == 0
     assert h.numpy().view(np.uint64).reshape(n, 2).tobytes() == exp.tobytes()
+
+
+
+# ------------------------------------------------------------------------------
+# presortedness: root segments whose sample is in order are checked in full and, if
+# they pass, finished as they stand or by one reversal; any defect falls back to the
+# full sort.  Every case is compared with the oracle and with the statistics.
+# ------------------------------------------------------------------------------
+
+def _presort_inputs(n):
+    i = np.arange(n, dtype=np.int64)
+    asc = (i - n // 2).astype(np.int32)
+    cases = {
+        "sorted": (asc.copy(), n),
+        "reversed": (asc[::-1].copy(), n),
+        "stair_steps": ((i // 1024).astype(np.int32), n),
+        "descending_runs": ((-(i // 777)).astype(np.int32), n),
+        "all_equal": (np.full(n, 7, np.int32), n),
+    }
+    last = asc.copy(); last[-2], last[-1] = last[-1], last[-2]
+    first = asc.copy(); first[0], first[1] = first[1], first[0]
+    mid = asc[::-1].copy(); mid[n // 2] = mid[0] + 5
+    cases["sorted_defect_at_end"] = (last, 0)
+    cases["sorted_defect_at_start"] = (first, 0)
+    cases["reversed_defect_in_middle"] = (mid, 0)
+    cases["nearly_sorted"] = (int32_pattern("nearly_sorted", n, seed=4), 0)
+    return cases
+
+
+@pytest.mark.parametrize("case", ["sorted", "reversed", "stair_steps", "descending_runs", "all_equal",
+                                  "sorted_defect_at_end", "sorted_defect_at_start",
+                                  "reversed_defect_in_middle", "nearly_sorted"])
+def test_presorted_inputs_match_oracle(T, orc, case):
+    n = 1_000_003
+    a, presorted = _presort_inputs(n)[case]
+    ctx = T.Context()
+    t = to_dev(a)
+    T.sort_(t, kind=1, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert from_dev(t, np.int32).tobytes() == oracle_sort(orc, a, 1).tobytes()
+    st = ctx.stats()
+    assert st["presorted_keys"] == presorted
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] + st["presorted_keys"] == n
+    ctx.close()
+
+
+def test_presorted_segments_mixed_with_others(T, orc):
+    rng = np.random.default_rng(8)
+    parts, offs, expect_pre = [], [0], 0
+    for k in range(40):
+        m = int(rng.integers(1, 60_000))
+        kind = k % 5
+        i = np.arange(m)
+        if kind == 0:
+            x = np.sort(rng.integers(-1000, 1000, m)).astype(np.int32)
+        elif kind == 1:
+            x = np.sort(rng.integers(-1000, 1000, m))[::-1].astype(np.int32)
+        elif kind == 2:
+            x = rng.integers(-2**31, 2**31 - 1, m).astype(np.int32)
+        elif kind == 3:
+            x = (i // 3).astype(np.int32)
+            if m > 10:
+                x[m // 2], x[m // 2 + 1] = x[m // 2 + 1] + 1, x[m // 2]
+        else:
+            x = np.zeros(m, np.int32)
+        if kind in (0, 1, 4) and m > 4096:
+            expect_pre += m
+        parts.append(x)
+        offs.append(offs[-1] + m)
+    a = np.concatenate(parts)
+    offs = np.array(offs, dtype=np.int64)
+    ctx = T.Context()
+    t = to_dev(a)
+    T.sort_segmented_(t, torch.from_numpy(offs).cuda(), kind=1, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    exp = a.copy()
+    orc.tsqs_sort_segments(exp, offs.astype(np.uint64), 1, threads=4)
+    assert from_dev(t, np.int32).tobytes() == exp.tobytes()
+    assert ctx.stats()["presorted_keys"] == expect_pre
+    ctx.close()
+
+
+def test_presorted_records_and_floats(T, orc):
+    n = 200_001
+    r = records_u64(n, seed=5)
+    r = r[np.lexsort((r[:, 1], r[:, 0]))][::-1].copy()          # descending (key, payload)
+    t = torch.from_numpy(r.view(np.int64).copy()).cuda()
+    T.sort_(t, records=True)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    assert t.cpu().numpy().view(np.uint64).reshape(n, 2).tobytes() == oracle_sort(orc, r, 7).tobytes()
+    f = floats_normal_specials(n, seed=6)
+    f = f[np.argsort(total_order_key_f32(f), kind="stable")].copy()   # ascending totalOrder
+    got = gpu_sort(T, f, 3)
+    assert got.tobytes() == oracle_sort(orc, f, 3).tobytes()
+    got = gpu_sort(T, f[::-1].copy(), 3)
+    assert got.tobytes() == oracle_sort(orc, f, 3).tobytes()
+
+
+@pytest.mark.parametrize("case", ["sorted", "reversed", "sorted_defect_at_end"])
+def test_presorted_host_array(T, orc, case):
+    n = 300_001
+    a, _ = _presort_inputs(n)[case]
+    exp = oracle_sort(orc, a, 1)
+    h = torch.from_numpy(a.copy()).pin_memory()
+    assert T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, 4, 1, None) == 0
+    assert h.numpy().tobytes() == exp.tobytes()
