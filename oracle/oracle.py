@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             L.orc_three_way_split.argtypes = [vp, vp, sz, i, vp, ctypes.POINTER(sz),
                                               ctypes.POINTER(sz), ctypes.POINTER(sz)]
             L.orc_compare.argtypes = [vp, vp, i]
+            L.orc_wide_sort.argtypes = [vp, sz, sz, sz, i, ctypes.POINTER(u64), ctypes.POINTER(u64)]
             L.orc_elem_size.argtypes = [i]
             L.orc_elem_size.restype = sz
             _lib = L
@@ -129,6 +130,19 @@ def tsqs_sort_rows(a: np.ndarray, kind: int, cfg: OracleCfg | None = None) -> di
     if lib().orc_tsqs_sort_rows(a.ctypes.data, rows, n, kind, ctypes.byref(c), ctypes.byref(st)):
         raise RuntimeError("oracle sort failed")
     return st.as_dict()
+
+
+def wide_sort(a: np.ndarray, elem_size: int, key_offset: int, kind: int) -> dict:
+    """Late-swap sort (Section VIII.H) of the raw bytes of ``a``, viewed as elements of
+    elem_size bytes with a key of ``kind`` at key_offset; returns the move and cycle
+    counts."""
+    if not a.flags.c_contiguous or a.nbytes % elem_size:
+        raise ValueError("wide arrays must be C-contiguous whole elements")
+    mv, cy = ctypes.c_uint64(), ctypes.c_uint64()
+    if lib().orc_wide_sort(a.ctypes.data, a.nbytes // elem_size, elem_size, key_offset, kind,
+                           ctypes.byref(mv), ctypes.byref(cy)):
+        raise RuntimeError("oracle wide sort failed")
+    return {"moves": mv.value, "cycles": cy.value}
 
 
 def tsqs_sort_segments(a: np.ndarray, offsets: np.ndarray, kind: int, threads: int = 1) -> None:

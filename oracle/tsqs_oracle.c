@@ -708,11 +708,12 @@ static void ts_sort_range(tctx *c, idx a, idx b, uint64_t depth) {
     }
 }
 
-static int ctx_init(tctx *c, void *base, size_t n, int key_kind, const orc_cfg *cfg,
-                    orc_stats *st) {
+static int ctx_init_cmp(tctx *c, void *base, size_t n, size_t ses, cmp_fn cmp,
+                        const orc_cfg *cfg, orc_stats *st) {
     memset(c, 0, sizeof(*c));
-    c->cmp = pick_cmp(key_kind, &c->ses);
-    if (!c->cmp) return -1;
+    c->cmp = cmp;
+    c->ses = ses;
+    if (!c->cmp || !c->ses) return -1;
     if (cfg) c->cfg = *cfg; else orc_default_cfg(&c->cfg);
     c->ar = (char *)base;
     c->st = st;
@@ -728,6 +729,13 @@ static int ctx_init(tctx *c, void *base, size_t n, int key_kind, const orc_cfg *
     /* Section V.C: one draw per sort call, dran in [0.5, 1.5) */
     c->dran = 0.5 + (double)pm_next(&c->zgen) / (double)PM_M;
     return 0;
+}
+
+static int ctx_init(tctx *c, void *base, size_t n, int key_kind, const orc_cfg *cfg,
+                    orc_stats *st) {
+    size_t ses;
+    cmp_fn f = pick_cmp(key_kind, &ses);
+    return ctx_init_cmp(c, base, n, ses, f, cfg, st);
 }
 
 static void ctx_free(tctx *c) { free(c->tar); free(c->p); }
@@ -792,6 +800,73 @@ int orc_tsqs_sort_segments(void *base, const uint64_t *offs, size_t nseg, int ke
     for (int k = 0; k < started; k++) pthread_join(t[k], NULL);
     free(t);
     return j.err;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Large elements: late swapping (Section VIII.H).  The array of element pointers is */
+/* sorted by Triple State QuickSort (the pointed-to keys decide; equal keys keep     */
+/* their original order, because the pointers themselves break the tie), then the    */
+/* elements are moved into place by following the cycles of the permutation, each   */
+/* cycle through one temporary element.                                              */
+/* ------------------------------------------------------------------------------ */
+
+static _Thread_local size_t g_wide_off;
+static _Thread_local cmp_fn g_wide_key;
+
+static int cmp_wide_ptr(const void *x, const void *y) {
+    const char *px = *(const char *const *)x, *py = *(const char *const *)y;
+    const int r = g_wide_key(px + g_wide_off, py + g_wide_off);
+    if (r) return r;
+    return px < py ? -1 : (px > py ? 1 : 0);
+}
+
+int orc_wide_sort(void *base, size_t n, size_t es, size_t key_off, int key_kind,
+                  uint64_t *moves_out, uint64_t *cycles_out) {
+    size_t ks;
+    cmp_fn key = pick_cmp(key_kind, &ks);
+    if (!key || key_kind == ORC_REC || key_off + ks > es) return -1;
+    if (moves_out) *moves_out = 0;
+    if (cycles_out) *cycles_out = 0;
+    if (n < 2) return 0;
+    char *b = (char *)base;
+    char **ptr = (char **)malloc(n * sizeof(char *));
+    unsigned char *placed = (unsigned char *)calloc(n, 1);
+    char *tmp = (char *)malloc(es);
+    if (!ptr || !placed || !tmp) { free(ptr); free(placed); free(tmp); return -1; }
+    for (size_t i = 0; i < n; i++) ptr[i] = b + i * es;
+    g_wide_off = key_off;
+    g_wide_key = key;
+    orc_stats st;
+    memset(&st, 0, sizeof(st));
+    tctx c;
+    if (ctx_init_cmp(&c, ptr, n, sizeof(char *), cmp_wide_ptr, NULL, &st)) {
+        free(ptr); free(placed); free(tmp); return -1;
+    }
+    ts_sort_range(&c, 0, (idx)n - 1, 0);
+    ctx_free(&c);
+    /* ptr[j] is the original place of the element that belongs at j */
+    uint64_t moves = 0, cycles = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (placed[i]) continue;
+        placed[i] = 1;
+        if (ptr[i] == b + i * es) continue;             /* already in place */
+        cycles++;
+        memcpy(tmp, b + i * es, es);
+        moves++;
+        size_t j = i;
+        for (;;) {
+            const size_t src = (size_t)(ptr[j] - b) / es;
+            if (src == i) { memcpy(b + j * es, tmp, es); moves++; break; }
+            memcpy(b + j * es, b + src * es, es);
+            moves++;
+            placed[src] = 1;
+            j = src;
+        }
+    }
+    if (moves_out) *moves_out = moves;
+    if (cycles_out) *cycles_out = cycles;
+    free(ptr); free(placed); free(tmp);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------------ */

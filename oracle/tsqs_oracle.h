@@ -108,6 +108,16 @@ int orc_tsqs_sort_rows(void *base, size_t nrows, size_t n, int key_kind,
 int orc_tsqs_sort_segments(void *base, const uint64_t *offs, size_t nseg, int key_kind,
                            int threads);
 
+/* Late swapping for large elements (Section VIII.H): base holds n elements of es
+ * bytes, each with a key of kind key_kind (ORC_I32..ORC_F64) at byte offset key_off.
+ * Sorts the array of element pointers with Triple State QuickSort (keys decide, equal
+ * keys keep their original order) and then moves every element into place along the
+ * cycles of the permutation, one temporary element per cycle.  Reports the element
+ * moves (n - fixed points + cycles) and the cycle count.  Returns 0, or -1 on bad
+ * arguments or allocation failure. */
+int orc_wide_sort(void *base, size_t n, size_t es, size_t key_off, int key_kind,
+                  uint64_t *moves_out, uint64_t *cycles_out);
+
 /* Textbook quicksort: uniformly random pivot per stage, Hoare partition that compares
  * every non-pivot element exactly once, no insertion sort.  Counts cmps and swaps
  * (exchanges of a misplaced pair; moving the pivot is not an exchange). */

@@ -32,6 +32,10 @@ MUTATIONS = {
     # copy-back of tar in State 3R moves the wrong way
     "3R_copyback_direction": ("while (i > 0) { i--; m--; ccopy(c, AR(c, m), TAR(c, i)); }",
                               "while (i > 0) { i--; m++; ccopy(c, AR(c, m), TAR(c, i)); }"),
+    # late swapping (VIII.H): equal keys no longer ordered by their original place
+    "wide_tie_unstable": ("return px < py ? -1 : (px > py ? 1 : 0);", "return 0;"),
+    # late swapping: a cycle member not marked placed is walked again
+    "wide_cycle_unmarked": ("            placed[src] = 1;\n", ""),
 }
 
 
@@ -88,6 +92,18 @@ def _exhaustive_fails(L) -> bool:
             lo, hi = lo.value, hi.value
             if not ((a[:lo + 1] < p).all() and (a[hi:] > p).all() and (a[lo + 1:hi] == p).all()):
                 return True
+    # late swapping of wide elements against the stable order (few distinct keys)
+    from tests.test_oracle_wide import _expected, _make
+    L.orc_wide_sort.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_size_t,
+                                ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)]
+    for n, es, off in ((7, 12, 0), (100, 16, 4), (1000, 24, 8)):
+        raw = _make(n, es, off, 1, seed=n, distinct=5)
+        got = raw.copy()
+        mv, cy = ctypes.c_uint64(), ctypes.c_uint64()
+        L.orc_wide_sort(got.ctypes.data, n, es, off, 1, ctypes.byref(mv), ctypes.byref(cy))
+        if got.tobytes() != _expected(raw, n, es, off, np.int32).tobytes():
+            return True
     return False
 
 
