@@ -124,6 +124,21 @@ int tsqs_sort_segmented(void *base, size_t nmemb_total, const uint64_t *d_seg_of
  * `stream` before returning. */
 int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
 
+/* Large elements (Section VIII.G-H, "late swapping"; the qsort of an array of wide
+ * structures).  base (device) holds nmemb elements of elem_size bytes; element i is
+ * ordered by the key of kind key_kind (TSQS_I32 .. TSQS_F64, not records) stored at byte
+ * offset key_offset inside it, under that kind's total order, and elements with equal
+ * keys keep their original order (the sort is stable, so the result is unique).
+ * elem_size must be a multiple of 4 and of the key size, key_offset a multiple of the
+ * key size with the key inside the element, base aligned to 4 and to the key size, and
+ * nmemb < 2^31; otherwise TSQS_EINVAL.  (key, index) records are sorted by the record
+ * path, then every element is moved once by a gather into library scratch
+ * (16 + elem_size bytes per element, kept until tsqs_free_storage) and copied back.
+ * Asynchronous on `stream`; TSQS_ENOMEM if the scratch cannot be allocated.  The paper
+ * switches to this scheme above 320-byte elements; here the caller chooses it. */
+int tsqs_sort_wide(void *base, size_t nmemb, size_t elem_size, size_t key_offset,
+                   int key_kind, void *stream);
+
 /* Frees the default context's device scratch (Section III.G:
  * FreeTripleStateQuickSortStorage).  Synchronises the device first. */
 void tsqs_free_storage(void);

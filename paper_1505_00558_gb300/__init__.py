@@ -85,6 +85,21 @@ def sort_(t, *, kind: int | None = None, records: bool = False, stream=None, ctx
     return t
 
 
+def sort_wide_(t, elem_size: int, key_offset: int, key_kind: int, *, stream=None):
+    """Sorts the wide elements held in tensor ``t`` (any dtype; ``t.numel() *
+    t.element_size()`` bytes = nmemb * elem_size) by the key of ``key_kind`` at
+    ``key_offset`` bytes inside each element, stably, in place on its device."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("sort_wide_ needs a contiguous CUDA tensor")
+    nbytes = t.numel() * t.element_size()
+    if elem_size <= 0 or nbytes % elem_size:
+        raise ValueError("tensor size is not a whole number of elements")
+    s = ctypes.c_void_p(_stream_handle(stream))
+    _check(lib().tsqs_sort_wide(ctypes.c_void_p(t.data_ptr()), nbytes // elem_size, elem_size,
+                                key_offset, key_kind, s), "tsqs_sort_wide")
+    return t
+
+
 def sort_segmented_(t, offsets, *, kind: int | None = None, records: bool = False,
                     stream=None, ctx=None):
     """Sorts every segment [offsets[s], offsets[s+1]) of ``t`` in place.  ``offsets`` is

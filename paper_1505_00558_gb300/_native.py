@@ -59,6 +59,7 @@ SIGNATURES = {
     "tsqs_sort_segmented": (_i, [_vp, _sz, _vp, _sz, _sz, _i, _vp]),
     "tsqs_sort_host": (_i, [_vp, _sz, _sz, _i, _vp]),
     "tsqs_sort_noalloc": (_i, [_vp, _sz, _sz, _i, _vp]),
+    "tsqs_sort_wide": (_i, [_vp, _sz, _sz, _sz, _i, _vp]),
     "tsqs_free_storage": (None, []),
     "tsqs_last_device_status": (_i, [_vp]),
     "tsqs_ctx_create": (_vp, [ctypes.POINTER(Plan)]),

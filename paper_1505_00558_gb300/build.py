@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsqs.so")
 
 SOURCES = ["tsqs_common.cu", "tsqs_k4.cu", "tsqs_k8.cu", "tsqs_k16.cu", "tsqs_host.cu",
-           "tsqs_autotune.cu", "tsqs_server.cu", "tsqs_noalloc.cu"]
+           "tsqs_autotune.cu", "tsqs_server.cu", "tsqs_noalloc.cu", "tsqs_wide.cu"]
 EXTRA: list[str] = []
 
 

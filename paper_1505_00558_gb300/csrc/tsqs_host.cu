@@ -141,6 +141,10 @@ struct tsqs_ctx {
     cudaEvent_t done_ev = nullptr;
     bool ev_valid = false;
     unsigned int *h_cont = nullptr;    // pinned word for the host-driven loop
+    char *wide_rec = nullptr;          // large elements: (key, index) records
+    size_t wide_rec_bytes = 0;
+    char *wide_tmp = nullptr;          // large elements: the gathered copy
+    size_t wide_tmp_bytes = 0;
     std::recursive_mutex mu;
 };
 
@@ -427,6 +431,8 @@ void tsqs_ctx_destroy(tsqs_ctx *c) {
             if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
         }
         if (c->scratch) cudaFree(c->scratch);
+        if (c->wide_rec) cudaFree(c->wide_rec);
+        if (c->wide_tmp) cudaFree(c->wide_tmp);
         if (c->d_job) cudaFree(c->d_job);
         if (c->d_ctl) cudaFree(c->d_ctl);
         if (c->done_ev) cudaEventDestroy(c->done_ev);
@@ -561,6 +567,51 @@ int tsqs_last_device_status(void *stream) {
     tsqs_ctx *c = default_ctx();
     if (!c) return TSQS_ENOMEM;
     return read_status(c, (cudaStream_t)stream, true);
+}
+
+int tsqs_sort_wide(void *base, size_t nmemb, size_t elem_size, size_t key_offset, int key_kind,
+                   void *stream) {
+    if (key_kind < TSQS_I32 || key_kind > TSQS_F64) return TSQS_EINVAL;
+    const size_t ks = kind_size(key_kind);
+    if (elem_size == 0 || elem_size % 4 || elem_size % ks || key_offset % ks ||
+        key_offset + ks > elem_size)
+        return TSQS_EINVAL;
+    if (nmemb > 1 && (!base || (uintptr_t)base % ks || (uintptr_t)base % 4)) return TSQS_EINVAL;
+    if (nmemb >= (1ull << 31)) return TSQS_EINVAL;
+    if (nmemb <= 1) return TSQS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    tsqs_ctx *c = default_ctx();
+    if (!c) return TSQS_ENOMEM;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int rc = ctx_init_device(c);
+    if (rc) return rc;
+    const size_t rec_bytes = nmemb * 16, tmp_bytes = nmemb * elem_size;
+    if (rec_bytes > c->wide_rec_bytes || tmp_bytes > c->wide_tmp_bytes) {
+        ctx_quiesce(c);
+        CK(cudaStreamSynchronize(s));
+        if (rec_bytes > c->wide_rec_bytes) {
+            if (c->wide_rec) cudaFree(c->wide_rec);
+            c->wide_rec = nullptr;
+            c->wide_rec_bytes = 0;
+            if (cudaMalloc((void **)&c->wide_rec, rec_bytes) != cudaSuccess) { cudaGetLastError(); return TSQS_ENOMEM; }
+            c->wide_rec_bytes = rec_bytes;
+        }
+        if (tmp_bytes > c->wide_tmp_bytes) {
+            if (c->wide_tmp) cudaFree(c->wide_tmp);
+            c->wide_tmp = nullptr;
+            c->wide_tmp_bytes = 0;
+            if (cudaMalloc((void **)&c->wide_tmp, tmp_bytes) != cudaSuccess) { cudaGetLastError(); return TSQS_ENOMEM; }
+            c->wide_tmp_bytes = tmp_bytes;
+        }
+    }
+    if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
+    if ((rc = wide_keys(key_kind, base, nmemb, elem_size, key_offset, c->wide_rec, c->sms, s))) return rc;
+    if ((rc = ctx_launch(c, c->wide_rec, nmemb, nullptr, 0, 16, TSQS_U64_U64_REC, s))) return rc;
+    if ((rc = wide_gather(base, nmemb, elem_size, c->wide_rec, c->wide_tmp, c->sms, s))) return rc;
+    CK(cudaMemcpyAsync(base, c->wide_tmp, tmp_bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(c->done_ev, s));
+    c->ev_valid = true;
+    return TSQS_OK;
 }
 
 void tsqs_debug_set_spin_limit(uint32_t polls) { g_debug_spin = polls; }

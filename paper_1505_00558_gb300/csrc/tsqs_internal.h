@@ -127,6 +127,13 @@ struct KindOps {
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
 };
 
+// Large elements (tsqs_wide.cu): (key, index) records of every element, and the gather
+// of the elements in record order.  `stream` is a cudaStream_t.
+int wide_keys(int kind, const void *base, uint64_t n, uint64_t es, uint64_t key_off, void *rec,
+              int sms, void *stream);
+int wide_gather(const void *src, uint64_t n, uint64_t es, const void *rec, void *dst, int sms,
+                void *stream);
+
 const KindOps *ops_k4(int kind);
 const KindOps *ops_k8(int kind);
 const KindOps *ops_k16(int kind);
