@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tsqs", choices=["tsqs", "reference"])
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "patterns", "c1", "records", "floats", "batched", "serving"])
+                    choices=["uniform", "patterns", "c1", "records", "floats", "batched", "serving", "wide"])
     ap.add_argument("--n", type=int, default=N_HEADLINE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -503,6 +503,38 @@ def other_workload(args, dist):
                   "p_min": pm, "alg_bytes": alg, "achieved_gbs": alg / (med * 1e-3) / 1e9,
                   "frac_of_measured": alg / (med * 1e-3) / 1e9 / hbm,
                   "roofline_mkeys": hbm * 1e9 / (2 * pm * es) / 1e6}}, ms=med)
+    elif w == "wide":
+        # large elements (Section VIII.G-H): 56-byte elements, int64 key at byte 8
+        n, es, off = 1 << 24, 56, 8
+        from workloads import rand_u64
+        raw = np.frombuffer(rand_u64(1, 800, n * es // 8).tobytes(), dtype=np.uint8).copy()
+        src = torch.from_numpy(raw).cuda()
+        del raw
+        ts = []
+        for r in range(args.warmup + max(3, min(args.steps, 10))):
+            wk = src.clone()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            T.sort_wide_(wk, es, off, T.TSQS_I64)
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        ok = T.last_device_status() == 0
+        keys = wk.view(-1, es)[:, off:off + 8].contiguous().view(torch.int64).view(-1)
+        ok = ok and bool((keys[1:] >= keys[:-1]).all().item())
+        med = statistics.median(ts)
+        pm = p_min(n)
+        # key pass (8 B read, 16 B write), record sort (P_min passes of 2 x 16 B), gather
+        # (16 B record + es read + es write), copy back (es read + es write)
+        alg = n * (24 + pm * 32 + 16 + 4 * es)
+        _line(args, dist, n / med / 1e3,
+              {"workload": "2^24 elements of 56 bytes, int64 key at byte 8, uniform random, tsqs_sort_wide",
+               "n": n, "elem_size": es},
+              {"sorted_status_ok": ok, "roofline_whole_sort": {
+                  "p_min_records": pm, "alg_bytes": alg, "achieved_gbs": alg / (med * 1e-3) / 1e9,
+                  "frac_of_measured": alg / (med * 1e-3) / 1e9 / hbm}}, ms=med)
     elif w == "batched":
         batched_workload(args, dist, torch, T)
     elif w == "serving":

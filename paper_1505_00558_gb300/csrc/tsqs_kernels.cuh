@@ -399,6 +399,7 @@ __global__ void k_check(const Job *__restrict__ job, Ctl *ctl) {
     const uint64_t n = job->n;
     const typename K::S *src = buffer<K>(job, 0);
     __shared__ uint64_t s_first;
+    __shared__ uint32_t s_flag;
     for (uint64_t c0 = (uint64_t)blockIdx.x * kPresortChunk; c0 < n; c0 += (uint64_t)gridDim.x * kPresortChunk) {
         const uint64_t c1 = min(c0 + (uint64_t)kPresortChunk, n);
         if (threadIdx.x == 0) s_first = root_of(job, c0);
@@ -407,8 +408,15 @@ __global__ void k_check(const Job *__restrict__ job, Ctl *ctl) {
             uint64_t b, e;
             root_bounds(job, s, b, e);
             if (b >= c1) break;
-            const uint32_t flag = *(volatile const uint32_t *)&job->presort[s];
-            if (flag == 0u || e <= c0 || e <= b) continue;
+            // another block may clear the flag at any moment: one thread reads it and the
+            // block acts on that one value, so every thread reaches the same barriers
+            if (threadIdx.x == 0) s_flag = *(volatile const uint32_t *)&job->presort[s];
+            __syncthreads();
+            const uint32_t flag = s_flag;
+            if (flag == 0u || e <= c0 || e <= b) {
+                __syncthreads();                         // s_flag read by all before reuse
+                continue;
+            }
             // pairs (i, i + 1) with i in [max(c0, b), min(c1, e - 1))
             const uint64_t i0 = max(c0, b), i1 = min(c1, e - 1);
             bool bad = false;
@@ -1407,9 +1415,12 @@ template <int KIND>
 __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
                             cudaGraphConditionalHandle handle, int use_handle, uint32_t) {
     using K = Key<KIND>;
-    __shared__ uint32_t s_last;
+    __shared__ uint32_t s_last, s_ok;
     const int par = ctl->level & 1;
-    const bool ok_state = *(volatile uint32_t *)&ctl->status == 0u;
+    // block-uniform: the loop below holds warp-wide shuffles and a block barrier follows
+    if (threadIdx.x == 0) s_ok = *(volatile uint32_t *)&ctl->status == 0u ? 1u : 0u;
+    __syncthreads();
+    const bool ok_state = s_ok != 0u;
     const uint32_t nf = min(ctl->nfront[par], job->cap_front);
     const int np = par ^ 1;
     const uint32_t lane = threadIdx.x & 31u;

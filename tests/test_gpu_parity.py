@@ -483,3 +483,31 @@ def test_presorted_host_array(T, orc, case):
     h = torch.from_numpy(a.copy()).pin_memory()
     assert T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, 4, 1, None) == 0
     assert h.numpy().tobytes() == exp.tobytes()
+
+
+def test_presorted_many_segments_checked_concurrently(T, orc):
+    """Thousands of candidate segments checked by many blocks at once, with defects at
+    random places: flags are cleared while other blocks are still checking."""
+    rng = np.random.default_rng(19)
+    parts, offs = [], [0]
+    for k in range(6000):
+        m = int(rng.integers(4097, 20_000))
+        x = np.sort(rng.integers(-10**6, 10**6, m)).astype(np.int32)
+        if k % 2:
+            x = x[::-1].copy()
+        if k % 3 == 0:
+            j = int(rng.integers(0, m - 1))
+            x[j], x[j + 1] = x[j + 1], x[j]
+            if x[j] == x[j + 1]:
+                x[j] += 1
+        parts.append(x)
+        offs.append(offs[-1] + m)
+    a = np.concatenate(parts)
+    offs = np.array(offs, dtype=np.int64)
+    t = to_dev(a)
+    T.sort_segmented_(t, torch.from_numpy(offs).cuda(), kind=1)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    exp = a.copy()
+    orc.tsqs_sort_segments(exp, offs.astype(np.uint64), 1, threads=4)
+    assert from_dev(t, np.int32).tobytes() == exp.tobytes()
