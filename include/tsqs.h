@@ -92,6 +92,7 @@ typedef struct {
     uint64_t leaf_items;       /* leaf work items processed                             */
     uint64_t presorted_keys;   /* keys of root segments found already in order or in
                                   reverse order (finished without a partition level)   */
+    uint64_t deep_sorted_keys; /* keys sorted by the depth guard's bitonic fallback      */
     uint32_t level_keys_count; /* entries used in level_keys                            */
     uint32_t pad;
     uint64_t level_keys[64];   /* keys partitioned at level i (first 64 levels)         */
@@ -241,6 +242,13 @@ int tsqs_debug_small_sort(void *base, size_t nmemb, size_t elem_size, int key_ki
  * context to give up after `polls` polls (0 restores the default).  Used by tests
  * to check that an expired wait surfaces as TSQS_ETIMEOUT. */
 void tsqs_debug_set_spin_limit(uint32_t polls);
+
+/* Sets the depth guard's level for sorts that start afterwards (every context): a
+ * segment that would be partitioned at this level or deeper is sorted by the bitonic
+ * fallback instead (Section V.B-C's worst-case mitigation).  0 restores the default,
+ * 2 ceil(log2 n) + 8, which sampled pivots never reach in practice; tests set a small
+ * value to run the fallback on ordinary inputs. */
+void tsqs_debug_set_deep_level(uint32_t level);
 
 /* When on != 0, partition tile 1 of every later level of the default context never
  * publishes its look-back word, so the waits of its successors must run into the

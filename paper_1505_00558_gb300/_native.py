@@ -34,7 +34,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_uint32), ("max_frontier", ctypes.c_uint32),
                 ("partition_keys", ctypes.c_uint64), ("leaf_sorted_keys", ctypes.c_uint64),
                 ("leaf_filled_keys", ctypes.c_uint64), ("leaf_items", ctypes.c_uint64),
-                ("presorted_keys", ctypes.c_uint64),
+                ("presorted_keys", ctypes.c_uint64), ("deep_sorted_keys", ctypes.c_uint64),
                 ("level_keys_count", ctypes.c_uint32), ("pad", ctypes.c_uint32),
                 ("level_keys", ctypes.c_uint64 * 64)]
 
@@ -81,6 +81,7 @@ SIGNATURES = {
     "tsqs_debug_partition": (_i, [_vp, _vp, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp]),
     "tsqs_debug_small_sort": (_i, [_vp, _sz, _sz, _i, _vp, _sz, _vp]),
     "tsqs_debug_set_spin_limit": (None, [_u32]),
+    "tsqs_debug_set_deep_level": (None, [_u32]),
     "tsqs_debug_withhold_publish": (None, [_i]),
     "tsqs_plan_autotune": (_i, [_i, _sz, _sz, _vp, ctypes.POINTER(Plan)]),
     "tsqs_plan_cache_save": (_i, [ctypes.c_char_p]),

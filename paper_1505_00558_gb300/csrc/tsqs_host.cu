@@ -53,7 +53,8 @@ size_t kind_size(int kind) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, presort_off, misc_off, total;
+    size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, presort_off,
+        deep_off, dtiles_off, dchunks_off, misc_off, total;
     uint32_t cap_front, cap_tiles, cap_leaves, leaf_defer;
 };
 
@@ -90,6 +91,9 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
     L.cursor_off = off;         off = align_up(off + cf * sizeof(unsigned long long), 256);
     L.presort_off = off;        off = align_up(off + (nseg ? nseg : 1) * sizeof(uint32_t), 256);
+    L.deep_off = off;           off = align_up(off + cf * sizeof(LeafItem), 256);
+    L.dtiles_off = off;         off = align_up(off + (cf + 1) * sizeof(uint32_t), 256);
+    L.dchunks_off = off;        off = align_up(off + (cf + 1) * sizeof(uint32_t), 256);
     L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
     L.total = off;
     return L;
@@ -122,6 +126,7 @@ void normalise_plan(tsqs_plan *p) {
 }
 
 uint32_t g_debug_spin = 0;        // 0 = default
+uint32_t g_debug_deep = 0;        // depth-guard level; 0 = default (2 log2 n + 8)
 int g_debug_withhold = 0;
 
 }  // namespace
@@ -178,6 +183,8 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     const int k = o->kind;
     if (c->attrs_set[k]) return TSQS_OK;
     CK(cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem));
+    CK(cudaFuncSetAttribute(o->k_deep_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem));
+    CK(cudaFuncSetAttribute(o->k_deep_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem));
     for (int v = 0; v < kPartVariants; v++)
         CK(cudaFuncSetAttribute(o->part[v].k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 o->part[v].smem));
@@ -242,6 +249,10 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->seg_done = (uint32_t *)(c->scratch + L.done_off);
     j->seg_cursor = (unsigned long long *)(c->scratch + L.cursor_off);
     j->presort = (uint32_t *)(c->scratch + L.presort_off);
+    j->deep = (LeafItem *)(c->scratch + L.deep_off);
+    j->deep_tiles = (uint32_t *)(c->scratch + L.dtiles_off);
+    j->deep_chunks = (uint32_t *)(c->scratch + L.dchunks_off);
+    j->cap_deep = L.cap_front;
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
@@ -255,6 +266,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     unsigned lg = 1;
     while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
     j->max_levels = 256u + 8u * lg;
+    j->deep_level = g_debug_deep ? g_debug_deep : 2u * lg + 8u;
     j->offset_mode = (c->plan.offset_mode == 1 || g_debug_withhold) ? 1u : 0u;
     j->tile = (uint32_t)part_of(o, c->plan).tile;
     j->seed = c->plan.seed;
@@ -340,12 +352,68 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.sharedMemBytes = (unsigned)o->leaf_smem;
     kp.kernelParams = argsl_last;
     CK(cudaGraphAddKernelNode(&n_last, g, &n_loop, 1, &kp));
+    // depth guard, beside the final leaf pass: prep, tile sorts, a WHILE over the stages
+    cudaGraphConditionalHandle hd;
+    CK(cudaGraphConditionalHandleCreate(&hd, g, 0, cudaGraphCondAssignDefault));
+    int use_hd = 1;
+    void *argsd[] = {&pj, &pc, &hd, &use_hd};
+    cudaGraphNode_t n_dprep, n_dtiles, n_dloop, n_dstage, n_dfin;
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_deep_prep;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(512);
+    kp.kernelParams = argsd;
+    CK(cudaGraphAddKernelNode(&n_dprep, g, &n_loop, 1, &kp));
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_deep_tiles;
+    kp.gridDim = dim3(c->sms * 2);
+    kp.blockDim = dim3(512);
+    kp.sharedMemBytes = (unsigned)o->deep_smem;
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_dtiles, g, &n_dprep, 1, &kp));
+    cudaGraphNodeParams dp{};
+    dp.type = cudaGraphNodeTypeConditional;
+    dp.conditional.handle = hd;
+    dp.conditional.type = cudaGraphCondTypeWhile;
+    dp.conditional.size = 1;
+    CK(cudaGraphAddNode(&n_dloop, g, &n_dtiles, nullptr, 1, &dp));
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_deep_stage;
+    kp.gridDim = dim3(c->sms * 2);
+    kp.blockDim = dim3(512);
+    kp.sharedMemBytes = (unsigned)o->deep_smem;
+    kp.kernelParams = argsd;
+    CK(cudaGraphAddKernelNode(&n_dstage, dp.conditional.phGraph_out[0], nullptr, 0, &kp));
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_deep_finish;
+    kp.gridDim = dim3(c->sms * 2);
+    kp.blockDim = dim3(512);
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_dfin, g, &n_dloop, 1, &kp));
 
     cudaGraphExec_t ex = nullptr;
     CK(cudaGraphInstantiate(&ex, g, 0));
     c->graph[k] = g;
     c->exec[k] = ex;
     return TSQS_OK;
+}
+
+// Depth guard, host-driven (the graph runs the same kernels under a WHILE node).
+cudaError_t run_deep_host(tsqs_ctx *c, const KindOps *o, cudaStream_t s, Job *pj, Ctl *pc) {
+    cudaGraphConditionalHandle hd = 0;
+    int use_hd = 0;
+    void *argsd[] = {&pj, &pc, &hd, &use_hd};
+    void *args2[] = {&pj, &pc};
+    cudaError_t e;
+    if ((e = cudaLaunchKernel(o->k_deep_prep, dim3(1), dim3(512), argsd, 0, s)) != cudaSuccess) return e;
+    if ((e = cudaLaunchKernel(o->k_deep_tiles, dim3(c->sms * 2), dim3(512), args2, (size_t)o->deep_smem, s)) != cudaSuccess) return e;
+    for (int it = 0; it < 4096; it++) {
+        if ((e = cudaMemcpyAsync(c->h_cont, &pc->deep_cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if (!*c->h_cont) break;
+        if ((e = cudaLaunchKernel(o->k_deep_stage, dim3(c->sms * 2), dim3(512), argsd, (size_t)o->deep_smem, s)) != cudaSuccess) return e;
+    }
+    return cudaLaunchKernel(o->k_deep_finish, dim3(c->sms * 2), dim3(512), args2, 0, s);
 }
 
 int validate(void *base, size_t nmemb, size_t elem_size, int key_kind) {
@@ -524,6 +592,7 @@ int tsqs_ctx_stats(tsqs_ctx *c, void *stream, tsqs_stats *out) {
     out->leaf_filled_keys = h.leaf_filled;
     out->leaf_items = h.leaf_items;
     out->presorted_keys = h.presorted;
+    out->deep_sorted_keys = h.deep_keys;
     const uint32_t nl = std::min<uint32_t>(h.level, (uint32_t)kStatLevels);
     out->level_keys_count = nl;
     for (uint32_t i = 0; i < nl; i++) out->level_keys[i] = h.level_keys[i];
@@ -615,6 +684,7 @@ int tsqs_sort_wide(void *base, size_t nmemb, size_t elem_size, size_t key_offset
 }
 
 void tsqs_debug_set_spin_limit(uint32_t polls) { g_debug_spin = polls; }
+void tsqs_debug_set_deep_level(uint32_t level) { g_debug_deep = level; }
 void tsqs_debug_withhold_publish(int on) { g_debug_withhold = on ? 1 : 0; }
 
 // ---------------------------------------------------------------------------------
@@ -741,6 +811,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
         CK(cudaEventElapsedTime(&lms, ev[2], ev[3]));
         h_leaf_ms[L - 1] += lms;
     }
+    CK(run_deep_host(c, o, s, c->d_job, c->d_ctl));
     for (auto &e : ev) cudaEventDestroy(e);
     if (h_keys) {
         Ctl hc;
@@ -897,6 +968,10 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     j->seg_done = (uint32_t *)(scratch + L.done_off);
     j->seg_cursor = (unsigned long long *)(scratch + L.cursor_off);
     j->presort = (uint32_t *)(scratch + L.presort_off);
+    j->deep = (LeafItem *)(scratch + L.deep_off);
+    j->deep_tiles = (uint32_t *)(scratch + L.dtiles_off);
+    j->deep_chunks = (uint32_t *)(scratch + L.dchunks_off);
+    j->cap_deep = L.cap_front;
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
@@ -909,6 +984,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     unsigned lg = 1;
     while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
     j->max_levels = 256u + 8u * lg;
+    j->deep_level = g_debug_deep ? g_debug_deep : 2u * lg + 8u;
     j->offset_mode = plan.offset_mode == 1 ? 1u : 0u;
     j->tile = (uint32_t)part_of(o, plan).tile;
     j->seed = plan.seed;

@@ -56,6 +56,11 @@ struct Ctl {
     uint32_t nleaf;           // leaf items queued (across levels, until a leaf pass)
     uint32_t leaf_blocks;     // leaf-pass blocks finished (last one empties the queue)
     uint32_t presort_any;     // some root segment's sample is in order (presortedness pass)
+    uint32_t ndeep;           // segments handed to the depth-guard sorter
+    uint32_t deep_kk, deep_jj;  // its next stage: merge width 2^kk, stride 2^jj (11: on-chip)
+    uint32_t deep_maxlog;     // log2 of the largest padded deep segment
+    uint32_t deep_blocks;     // stage-kernel blocks finished (the last one advances the stage)
+    uint32_t deep_cont;       // more stages (host-driven mode reads it)
     uint32_t max_front;
     uint32_t levels_done;
     uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
@@ -64,6 +69,7 @@ struct Ctl {
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;
     uint64_t presorted;       // keys of root segments found already in order (or reversed)
+    uint64_t deep_keys;       // keys sorted by the depth-guard sorter
     uint64_t level_keys[kStatLevels];
 };
 
@@ -84,8 +90,14 @@ struct Job {
     unsigned long long *seg_cursor;    // reserved (#<p | #>p << 32) per frontier segment
     uint32_t *presort;        // per root segment: 0, or 1 / 2 while it may be / is known to be
                               // non-decreasing / non-increasing
+    LeafItem *deep;           // segments that reached deep_level (kind flag: buffer 1)
+    uint32_t *deep_tiles;     // prefix over deep segments of their 4096-element tiles
+    uint32_t *deep_chunks;    // prefix over deep segments of their pair chunks
     uint32_t cap_front, cap_tiles, cap_leaves;
     uint32_t leaf_defer;      // a level's leaf pass runs only above this many queued items
+    uint32_t cap_deep;        // capacity of deep (segments above small_T are disjoint)
+    uint32_t deep_level;      // a child that would be partitioned at this level or later goes
+                              // to the depth-guard sorter instead
     uint32_t small_T;         // on-chip threshold
     uint32_t samples;         // pivot sample count (odd, <= kMaxSamples)
     uint32_t vec_off;         // (address of base / elem_size) mod (16 / elem_size)
@@ -124,6 +136,8 @@ struct KindOps {
     PartVariant part[kPartVariants];   // [0] is the default shape
     const void *k_init, *k_leaf, *k_pivot, *k_finish;
     const void *k_orient, *k_check, *k_presort;
+    const void *k_deep_prep, *k_deep_tiles, *k_deep_stage, *k_deep_finish;
+    int deep_smem;            // dynamic shared memory of the on-chip deep stages
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
 };
 

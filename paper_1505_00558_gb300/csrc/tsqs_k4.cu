@@ -34,6 +34,11 @@ KindOps make_ops() {
     o.k_orient = (const void *)k_orient<KIND>;
     o.k_check = (const void *)k_check<KIND>;
     o.k_presort = (const void *)k_presort<KIND>;
+    o.k_deep_prep = (const void *)k_deep_prep<KIND>;
+    o.k_deep_tiles = (const void *)k_deep_tiles<KIND>;
+    o.k_deep_stage = (const void *)k_deep_stage<KIND>;
+    o.k_deep_finish = (const void *)k_deep_finish<KIND>;
+    o.deep_smem = (int)((kDeepTile + kDeepTile / 32) * sizeof(typename Key<KIND>::C));
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 4>;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;

@@ -1384,6 +1384,244 @@ __global__ void k_dbg_pivot(const Job *__restrict__ job, Ctl *ctl) {
         *reinterpret_cast<typename K::S *>(job->dbg_pivot_out) = K::uncanon(p);
 }
 
+// ---------------------------------------------------------------------------------
+// Depth guard (the worst-case mitigation of Section V.B-C: seeded sample jitter plus a
+// bounded depth, after which the segment goes to a sorter whose cost does not depend on
+// the pivots -- the introsort idea the paper cites).  A segment that would be
+// partitioned at deep_level or later is sorted in place, in the buffer that holds it,
+// by a bitonic network in mirror form over its length padded to a power of two; the
+// padding is virtual (+infinity, which never moves in mirror form), so only the real
+// elements are stored.  Every 4096-element tile is first sorted on chip; each larger
+// merge then takes one global pass per stride >= 4096 and one on-chip pass for the
+// strides below 4096.  O(n log^2 n) whatever the input.
+// ---------------------------------------------------------------------------------
+
+constexpr int kDeepTile = 4096;
+constexpr uint32_t kDeepChunk = 2048;    // pairs per block step of a global stage
+constexpr int kDeepThreads = 512;
+
+__device__ __forceinline__ uint32_t deep_log2(uint64_t m) {
+    uint32_t l = 0;
+    while ((1ull << l) < m) l++;
+    return l;
+}
+
+// Deep segment holding prefix entry x of `pre` (pre has nd + 1 entries), by binary search.
+__device__ __forceinline__ uint32_t deep_find(const uint32_t *pre, uint32_t nd, uint32_t x) {
+    uint32_t lo = 0, hi = nd;                 // pre[lo] <= x < pre[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One block: prefix sums of the deep segments' tiles and global-stage pair chunks, and
+// the first stage.
+template <int KIND>
+__global__ void k_deep_prep(const Job *__restrict__ job, Ctl *ctl, cudaGraphConditionalHandle h,
+                            int use_handle) {
+    __shared__ uint32_t s_t[kDeepThreads], s_c[kDeepThreads], s_l[kDeepThreads];
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    const uint32_t t = threadIdx.x, per = (nd + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = min(nd, t * per), b = min(nd, a + per);
+    uint32_t st = 0, sc = 0, ml = 0;
+    for (uint32_t s = a; s < b; s++) {
+        const uint64_t len = job->deep[s].len;
+        const uint32_t lg = deep_log2(len);
+        st += (uint32_t)((len + kDeepTile - 1) / kDeepTile);
+        sc += (uint32_t)(((1ull << lg) / 2 + kDeepChunk - 1) / kDeepChunk);
+        ml = max(ml, lg);
+    }
+    s_t[t] = st; s_c[t] = sc; s_l[t] = ml;
+    __syncthreads();
+    if (t == 0) {                                          // exclusive scan over threads
+        uint32_t at = 0, ac = 0, al = 0;
+        for (uint32_t k = 0; k < blockDim.x; k++) {
+            const uint32_t x = s_t[k], y = s_c[k];
+            s_t[k] = at; s_c[k] = ac;
+            at += x; ac += y; al = max(al, s_l[k]);
+        }
+        job->deep_tiles[nd] = at;
+        job->deep_chunks[nd] = ac;
+        ctl->deep_maxlog = al;
+        ctl->deep_kk = 13u;                                // first merge above one tile
+        ctl->deep_jj = 12u;                                // its mirror stage (stride 2^12)
+        ctl->deep_blocks = 0u;
+        const uint32_t cont = (nd > 0u && al >= 13u && ctl->status == 0u) ? 1u : 0u;
+        ctl->deep_cont = cont;
+        if (use_handle) cudaGraphSetConditional(h, cont);
+    }
+    __syncthreads();
+    uint32_t at = s_t[t], ac = s_c[t];
+    for (uint32_t s = a; s < b; s++) {
+        const uint64_t len = job->deep[s].len;
+        job->deep_tiles[s] = at;
+        job->deep_chunks[s] = ac;
+        at += (uint32_t)((len + kDeepTile - 1) / kDeepTile);
+        ac += (uint32_t)(((1ull << deep_log2(len)) / 2 + kDeepChunk - 1) / kDeepChunk);
+    }
+}
+
+// Shared-memory bitonic steps on one 4096-element tile (padded layout, +inf beyond cnt):
+// merges of width 2 .. kk_hi in full (kk_hi = 4096) or only the half-cleaners of
+// strides 2048 .. 1 (full = false).
+template <class C>
+__device__ __forceinline__ void deep_tile_network(C *sm, bool full) {
+    const uint32_t t = threadIdx.x;
+    for (uint32_t k = full ? 2u : (uint32_t)kDeepTile * 2u; k <= (uint32_t)kDeepTile * 2u; k <<= 1) {
+        if (full && k <= (uint32_t)kDeepTile) {
+            for (uint32_t q = t; q < (uint32_t)kDeepTile / 2; q += blockDim.x) {    // mirror
+                const uint32_t half = k >> 1, i = (q / half) * k + (q % half), p = i ^ (k - 1u);
+                cx(sm[pad32(i)], sm[pad32(p)]);
+            }
+            __syncthreads();
+        }
+        const uint32_t jtop = (full && k <= (uint32_t)kDeepTile) ? k >> 2 : (uint32_t)kDeepTile / 2;
+        for (uint32_t j = jtop; j >= 1u; j >>= 1) {
+            for (uint32_t q = t; q < (uint32_t)kDeepTile / 2; q += blockDim.x) {
+                const uint32_t i = (q / j) * 2u * j + (q % j);
+                cx(sm[pad32(i)], sm[pad32(i + j)]);
+            }
+            __syncthreads();
+        }
+        if (!full || k == (uint32_t)kDeepTile) break;
+    }
+}
+
+// Loads tile ti of deep segment `it` into sm (canonical keys, +inf padding), runs the
+// network, stores the real elements back.
+template <int KIND>
+__device__ __forceinline__ void deep_tile(const Job *job, const LeafItem &it, uint32_t ti,
+                                          typename Key<KIND>::C *sm, bool full) {
+    using K = Key<KIND>;
+    typename K::S *buf = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0) + it.begin;
+    const uint64_t base = (uint64_t)ti * kDeepTile;
+    const uint32_t cnt = (uint32_t)min((uint64_t)kDeepTile, (uint64_t)it.len - base);
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kDeepTile; i += blockDim.x)
+        sm[pad32(i)] = i < cnt ? K::canon(buf[base + i]) : c_max<typename K::C>();
+    __syncthreads();
+    deep_tile_network(sm, full);
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) buf[base + i] = K::uncanon(sm[pad32(i)]);
+    __syncthreads();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kDeepThreads) k_deep_tiles(const Job *__restrict__ job, Ctl *ctl) {
+    using C = typename Key<KIND>::C;
+    extern __shared__ __align__(16) unsigned char deep_raw[];
+    C *sm = reinterpret_cast<C *>(deep_raw);
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    if (nd == 0u) return;
+    const uint32_t total = job->deep_tiles[nd];
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x == 0) s_seg = deep_find(job->deep_tiles, nd, t);
+        __syncthreads();
+        const uint32_t s = s_seg;
+        const LeafItem it = job->deep[s];
+        deep_tile<KIND>(job, it, t - job->deep_tiles[s], sm, true);
+    }
+}
+
+// One stage for every deep segment whose padded length reaches the current merge width;
+// the last block to finish advances the stage and sets the loop condition.
+template <int KIND>
+__global__ void __launch_bounds__(kDeepThreads) k_deep_stage(const Job *__restrict__ job, Ctl *ctl,
+                                                             cudaGraphConditionalHandle h, int use_handle) {
+    using K = Key<KIND>;
+    using C = typename K::C;
+    using S = typename K::S;
+    extern __shared__ __align__(16) unsigned char deep_raw[];
+    C *sm = reinterpret_cast<C *>(deep_raw);
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    const uint32_t kk = ctl->deep_kk, jj = ctl->deep_jj;
+    if (jj >= 12u) {                                      // a global stride
+        const uint32_t total = job->deep_chunks[nd];
+        const bool mirror = jj == kk - 1u;
+        for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+            if (threadIdx.x == 0) s_seg = deep_find(job->deep_chunks, nd, c);
+            __syncthreads();
+            const uint32_t s = s_seg;
+            __syncthreads();
+            const LeafItem it = job->deep[s];
+            const uint64_t len = it.len, P = 1ull << deep_log2(len);
+            if (P < (1ull << kk)) continue;
+            S *buf = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0) + it.begin;
+            const uint64_t q0 = (uint64_t)(c - job->deep_chunks[s]) * kDeepChunk;
+            const uint64_t q1 = min(q0 + kDeepChunk, P / 2);
+            for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+                uint64_t i, p;
+                if (mirror) {
+                    i = ((q >> (kk - 1u)) << kk) | (q & ((1ull << (kk - 1u)) - 1u));
+                    p = i ^ ((1ull << kk) - 1u);
+                } else {
+                    i = ((q >> jj) << (jj + 1u)) | (q & ((1ull << jj) - 1u));
+                    p = i + (1ull << jj);
+                }
+                if (p < len) {                            // p beyond the end is +infinity
+                    const S x = buf[i], y = buf[p];
+                    if (c_lt(K::canon(y), K::canon(x))) { buf[i] = y; buf[p] = x; }
+                }
+            }
+        }
+    } else {                                              // strides 2048 .. 1, on chip
+        const uint32_t total = job->deep_tiles[nd];
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+            if (threadIdx.x == 0) s_seg = deep_find(job->deep_tiles, nd, t);
+            __syncthreads();
+            const uint32_t s = s_seg;
+            const LeafItem it = job->deep[s];
+            if ((1ull << deep_log2(it.len)) < (1ull << kk)) { __syncthreads(); continue; }
+            deep_tile<KIND>(job, it, t - job->deep_tiles[s], sm, false);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->deep_blocks, 1u) + 1u == gridDim.x) {
+            uint32_t nk = kk, nj = jj;
+            if (nj > 12u) nj--;                           // next global half-cleaner
+            else if (nj == 12u) nj = 11u;                 // then the on-chip strides
+            else { nk++; nj = nk - 1u; }                  // then the next merge's mirror
+            const uint32_t cont = (nk <= ctl->deep_maxlog && ctl->status == 0u) ? 1u : 0u;
+            ctl->deep_kk = nk;
+            ctl->deep_jj = nj;
+            ctl->deep_blocks = 0u;
+            ctl->deep_cont = cont;
+            if (use_handle) cudaGraphSetConditional(h, cont);
+        }
+    }
+}
+
+// Moves every deep segment to the output array when its buffer is not the output.
+template <int KIND>
+__global__ void k_deep_finish(const Job *__restrict__ job, Ctl *ctl) {
+    using K = Key<KIND>;
+    using S = typename K::S;
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    if (nd == 0u) return;
+    const uint32_t total = job->deep_tiles[nd];
+    S *out = reinterpret_cast<S *>(job->out);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x == 0) s_seg = deep_find(job->deep_tiles, nd, t);
+        __syncthreads();
+        const uint32_t s = s_seg;
+        __syncthreads();
+        const LeafItem it = job->deep[s];
+        const uint32_t ti = t - job->deep_tiles[s];
+        if (threadIdx.x == 0 && ti == 0)
+            atomicAdd((unsigned long long *)&ctl->deep_keys, (unsigned long long)it.len);
+        const S *buf = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0);
+        if ((const void *)buf == job->out) continue;
+        const uint64_t base = it.begin + (uint64_t)ti * kDeepTile;
+        const uint64_t end = min(base + (uint64_t)kDeepTile, (uint64_t)it.begin + it.len);
+        for (uint64_t i = base + threadIdx.x; i < end; i += blockDim.x) out[i] = buf[i];
+    }
+}
+
 // Level control (one thread).  Records the level's statistics, resets the consumed
 // queues, advances the level and sets the loop condition.
 __device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGraphConditionalHandle handle,
@@ -1426,6 +1664,9 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t T = job->small_T;
     const int TILE = (int)job->tile;
+    // depth guard: a child that would be partitioned at deep_level or later goes to the
+    // bitonic sorter after the loop (this level is ctl->level, its children's is + 1)
+    const bool to_deep = ctl->level + 1u >= job->deep_level;
     // every lane takes one segment; a warp makes one atomic per counter for all its
     // pushes (frontier entries, tiles, leaf items, keys) and hands out the offsets
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -1454,14 +1695,16 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(ctl, TSQS_EINTERNAL);
         // per lane: up to two frontier pushes, two leaf pushes, and nch fill items
-        uint32_t nfr = 0, ntl = 0, nlf = 0;
+        uint32_t nfr = 0, ntl = 0, nlf = 0, ndp = 0;
         uint64_t keys = 0;
         int64_t s0[2] = {0, 0};
         uint32_t ntc[2] = {0, 0};
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const uint64_t msz = ce[c] - cb[c];
-            if (msz > T) {
+            if (msz > T && to_deep) {
+                ndp++;
+            } else if (msz > T) {
                 s0[c] = tile_origin<K::V>(cb[c], job->vec_off);
                 ntc[c] = tiles_for(ce[c], s0[c], TILE);
                 nfr++; ntl += ntc[c]; keys += msz;
@@ -1482,13 +1725,14 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
         }
         nlf += nch;
         // warp-exclusive offsets and one atomic per counter
-        uint32_t xf = nfr, xt = ntl, xl = nlf;
+        uint32_t xf = nfr, xt = ntl, xl = nlf, xd = ndp;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t a = __shfl_up_sync(0xffffffffu, xf, o);
             const uint32_t b2 = __shfl_up_sync(0xffffffffu, xt, o);
             const uint32_t c2 = __shfl_up_sync(0xffffffffu, xl, o);
-            if (lane >= (uint32_t)o) { xf += a; xt += b2; xl += c2; }
+            const uint32_t d2 = __shfl_up_sync(0xffffffffu, xd, o);
+            if (lane >= (uint32_t)o) { xf += a; xt += b2; xl += c2; xd += d2; }
         }
         uint64_t ksum = keys, fsum = ifill;
 #pragma unroll
@@ -1496,23 +1740,35 @@ __global__ void k_level_end(const Job *__restrict__ job, Ctl *ctl,
             ksum += __shfl_xor_sync(0xffffffffu, ksum, o);
             fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
         }
-        uint32_t bf = 0, bt = 0, bl = 0;
+        uint32_t bf = 0, bt = 0, bl = 0, bd = 0;
         if (lane == 31) {
             bf = atomicAdd(&ctl->nfront[np], xf);
             bt = atomicAdd(&ctl->ntiles[np], xt);
             bl = atomicAdd(&ctl->nleaf, xl);
+            if (xd) bd = atomicAdd(&ctl->ndeep, xd);
             if (ksum) atomicAdd((unsigned long long *)&ctl->front_keys[np], (unsigned long long)ksum);
             if (fsum) atomicAdd((unsigned long long *)&ctl->leaf_filled, (unsigned long long)fsum);
         }
         bf = __shfl_sync(0xffffffffu, bf, 31) + xf - nfr;
         bt = __shfl_sync(0xffffffffu, bt, 31) + xt - ntl;
         bl = __shfl_sync(0xffffffffu, bl, 31) + xl - nlf;
+        bd = __shfl_sync(0xffffffffu, bd, 31) + xd - ndp;
         // write this lane's pushes
         bool overflow = false;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const uint64_t msz = ce[c] - cb[c];
-            if (msz > T) {
+            if (msz > T && to_deep) {
+                if (bd >= job->cap_deep) overflow = true;
+                else {
+                    LeafItem it;
+                    it.begin = cb[c]; it.len = (uint32_t)msz;
+                    it.kind = np ? kLeafInAlt : 0u;      // keys in the buffer this level wrote
+                    it.v_lo = 0; it.v_hi = 0;
+                    job->deep[bd] = it;
+                }
+                bd++;
+            } else if (msz > T) {
                 if (bf >= job->cap_front || (uint64_t)bt + ntc[c] > job->cap_tiles) {
                     overflow = true;
                 } else {

@@ -78,6 +78,8 @@ int setup_device(int dev, DevState &d) {
             return TSQS_EINTERNAL;
         int occ_p = 0, occ_l = 0;
         if (cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem) != cudaSuccess ||
+            cudaFuncSetAttribute(o->k_deep_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem) != cudaSuccess ||
+            cudaFuncSetAttribute(o->k_deep_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem) != cudaSuccess ||
             cudaFuncSetAttribute(pv.k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, pv.smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pv.k_partition, pv.threads, pv.smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem) != cudaSuccess) {
@@ -150,6 +152,22 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
     // the final leaf pass over every queued item
     if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl_last,
                          (size_t)o->leaf_smem, s) != cudaSuccess)
+        return TSQS_ECUDA;
+    // depth guard: segments that reached the level bound are sorted by the bitonic stages
+    int use_hd = 0;
+    void *argsd[] = {&pj, &pc, &h, &use_hd};
+    if (cudaLaunchKernel(o->k_deep_prep, dim3(1), dim3(512), argsd, 0, s) != cudaSuccess ||
+        cudaLaunchKernel(o->k_deep_tiles, dim3(d.sms * 2), dim3(512), args2, (size_t)o->deep_smem, s) != cudaSuccess)
+        return TSQS_ECUDA;
+    for (int it = 0; it < 4096; it++) {
+        if (cudaMemcpyAsync(&g_cont[dev], &d.ctl->deep_cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return TSQS_ECUDA;
+        if (!g_cont[dev]) break;
+        if (cudaLaunchKernel(o->k_deep_stage, dim3(d.sms * 2), dim3(512), argsd, (size_t)o->deep_smem, s) != cudaSuccess)
+            return TSQS_ECUDA;
+    }
+    if (cudaLaunchKernel(o->k_deep_finish, dim3(d.sms * 2), dim3(512), args2, 0, s) != cudaSuccess)
         return TSQS_ECUDA;
     uint32_t status = 0;
     if (cudaMemcpyAsync(&status, &d.ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
