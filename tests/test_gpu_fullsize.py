@@ -1,0 +1,135 @@
+"""The benchmark configurations at full size, through the same entry points the bench
+times (tsqs_sort / tsqs_sort_segmented on the default context, one graph launch).
+
+At these sizes the output is checked three ways, none of which uses the CUDA path:
+  - element by element against the CPU oracle where it finishes in seconds (2^27
+    uniform int32: about 20 s single-threaded);
+  - at sampled positions k, one by one from the definition of the sorted order: the
+    element at k has fewer than k + 1 input elements below it and more than k at or
+    below it (counted on the CPU over the input);
+  - by properties that hold at any size: adjacent elements in order, and the sorted
+    multiset equal to that of the input (a library sort of the input on the device).
+"""
+import numpy as np
+import pytest
+
+from workloads import PATTERNS, int32_pattern, records_u64, floats_normal_specials, total_order_key_f32
+from workloads.patterns import batched_segments, batched_keys
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1505_00558_gb300 as T
+    T.lib()
+    return T
+
+
+def _sampled_ranks_ok(order_key_in: np.ndarray, order_key_out_at, ks) -> None:
+    """order_key_in: totally ordered integer image of the input (numpy); for each k the
+    output element's image v must satisfy #(in < v) <= k < #(in <= v)."""
+    for k in ks:
+        v = order_key_out_at(k)
+        lt = int(np.count_nonzero(order_key_in < v))
+        le = int(np.count_nonzero(order_key_in <= v))
+        assert lt <= k < le, f"rank check failed at {k}"
+
+
+def _ks(n, seed, m=40):
+    rng = np.random.default_rng(seed)
+    return sorted(set([0, 1, n // 2, n - 2, n - 1] + [int(x) for x in rng.integers(0, n, m)]))
+
+
+def test_full_2e27_uniform_int32_matches_oracle(T, orc):
+    n = 1 << 27
+    a = int32_pattern("random", n, seed=1)
+    t = torch.from_numpy(a).cuda()
+    T.sort_(t)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    got = t.cpu().numpy()
+    exp = a.copy()
+    orc.tsqs_sort(exp, 1)
+    assert got.tobytes() == exp.tobytes()
+    _sampled_ranks_ok(a, lambda k: got[k], _ks(n, 1))
+
+
+@pytest.mark.parametrize("pattern", PATTERNS[1:])
+def test_full_2e27_patterns(T, pattern):
+    n = 1 << 27
+    a = int32_pattern(pattern, n, seed=1)
+    src = torch.from_numpy(a).cuda()
+    t = src.clone()
+    T.sort_(t)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    assert bool((t[1:] >= t[:-1]).all().item())
+    assert torch.equal(t, torch.sort(src)[0])
+    got = t.cpu().numpy()
+    _sampled_ranks_ok(a, lambda k: got[k], _ks(n, 2, m=12))
+
+
+def test_full_2e26_records(T):
+    n = 1 << 26
+    r = records_u64(n, seed=1)
+    t = torch.from_numpy(r.view(np.int64).copy()).cuda()
+    T.sort_(t, records=True)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    got = t.cpu().numpy().view(np.uint64).reshape(n, 2)
+    # in order by (key, payload)
+    k, p = got[:, 0], got[:, 1]
+    assert bool(np.all((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (p[1:] >= p[:-1]))))
+    # same multiset: identical after a lexicographic library sort of the input
+    idx = np.lexsort((r[:, 1], r[:, 0]))
+    assert got.tobytes() == r[idx].tobytes()
+
+
+def test_full_2e26_floats_total_order(T):
+    n = 1 << 26
+    f = floats_normal_specials(n, seed=1)
+    t = torch.from_numpy(f.copy()).cuda()
+    T.sort_(t, kind=3)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    got = t.cpu().numpy()
+    kin = total_order_key_f32(f)
+    kout = total_order_key_f32(got)
+    assert bool(np.all(kout[1:] >= kout[:-1]))
+    assert np.array_equal(np.sort(kin), kout)
+    _sampled_ranks_ok(kin, lambda k: kout[k], _ks(n, 3))
+
+
+def test_full_batched_20000_segments(T, orc):
+    nseg = 20_000
+    offs, sizes, pat = batched_segments(nseg, seed=1)
+    x = batched_keys(offs, pat, seed=1)
+    src = torch.from_numpy(x).cuda()
+    d_offs = torch.from_numpy(offs.astype(np.int64)).cuda()
+    t = src.clone()
+    T.sort_segmented_(t, d_offs, kind=1)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    # every segment in order, and each segment the same multiset: (segment, key) pairs
+    # of output and input agree after a library sort
+    seg = torch.repeat_interleave(torch.arange(nseg, device="cuda", dtype=torch.int64),
+                                  torch.from_numpy(np.diff(offs).astype(np.int64)).cuda())
+    comb_out = (seg << 32) | (t.to(torch.int64) + 2**31)
+    assert bool((comb_out[1:] >= comb_out[:-1]).all().item())
+    comb_in = (seg << 32) | (src.to(torch.int64) + 2**31)
+    assert torch.equal(torch.sort(comb_in)[0], comb_out)
+    del comb_in, comb_out, seg
+    # sampled segments against the oracle, element by element
+    rng = np.random.default_rng(4)
+    got = t.cpu().numpy()
+    big = int(np.argmax(np.diff(offs)))
+    for s in sorted(set([0, nseg - 1, big] + [int(v) for v in rng.integers(0, nseg, 25)])):
+        b, e = int(offs[s]), int(offs[s + 1])
+        exp = x[b:e].copy()
+        orc.tsqs_sort(exp, 1)
+        assert got[b:e].tobytes() == exp.tobytes(), f"segment {s}"
