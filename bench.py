@@ -41,7 +41,11 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one partition launch per key it read,
 # from an ncu capture of the kernel source with this sha256 prefix (null when the
 # kernel changed since).
-NCU_TRAFFIC = {"kernels_sha": None, "bytes_per_key": None, "source": None}
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-width k_partition launch at the
+# headline size (2^27 int32, level 3 of an instrumented sort): 537.0 MB + 480.2 MB for
+# 134,217,721 keys; valid only for the kernel source it was taken on
+NCU_TRAFFIC = {"kernels_sha": "cd31b65f9bf709a1", "bytes_per_key": (537026304 + 480212224) / 134217721,
+               "source": "profiles/k_partition_2e27_int32_traffic.md"}
 
 
 def parse():
