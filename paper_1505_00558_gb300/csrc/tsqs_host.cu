@@ -3,9 +3,11 @@
 // A context owns one block of device scratch (the second buffer of the ping-pong,
 // the work queues and the look-back words; the analogue of the persistent temporary
 // storage of Section III.G) and one CUDA graph per key kind.  The graph is
-//     init  ->  while (queues not empty) { leaf ; pivot ; partition ; finish }
-// with the loop condition set on the device by the finish kernel, so a whole sort is
-// one graph launch with no host round trip between levels.  Every kernel reads the
+//     orient -> check -> presort -> init
+//       -> while (frontier not empty) { leaf ; pivot ; partition ; level end }
+//       -> final leaf pass   ||   deep prep -> deep tiles -> while (stages) { deep stage } -> deep finish
+// with the loop conditions set on the device (by the level-end and deep-stage kernels),
+// so a whole sort is one graph launch with no host round trip between levels.  Every kernel reads the
 // per-call description (Job) from device memory, written by a one-thread setup kernel
 // launched just before the graph, so the same graph serves every array of its kind.
 #include <cuda_runtime.h>
