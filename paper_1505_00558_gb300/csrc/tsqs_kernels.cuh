@@ -1187,8 +1187,8 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
     __syncthreads();
 }
 
-// Shared-memory layout of the leaf kernel: the padded sort buffer, then two raw
-// prefetch slots (a leaf's 16-byte-aligned hull) and their mbarriers.
+// Shared-memory layout of the leaf kernel: the padded sort buffer, then the raw
+// prefetch slot (the next item's 16-byte-aligned hull) and its mbarrier.
 template <int KIND>
 struct LeafLayout {
     using S = typename Key<KIND>::S;
@@ -1196,8 +1196,11 @@ struct LeafLayout {
     static constexpr int PRE = kMaxSmall + 2 * Key<KIND>::V;          // elements per slot
     static constexpr size_t sort_bytes = ((kMaxSmall + kMaxSmall / 32) * sizeof(C) + 127) / 128 * 128;
     static constexpr size_t off_pre = sort_bytes;
-    static constexpr size_t off_bar = off_pre + 2 * (size_t)PRE * sizeof(S);
-    static constexpr size_t bytes = off_bar + 2 * sizeof(unsigned long long);
+    // one prefetch slot: an item's keys leave it for the sort buffer before the next
+    // item's bulk copy is issued into it, so a second slot would only cost occupancy
+    static constexpr int NSLOT = 1;
+    static constexpr size_t off_bar = off_pre + NSLOT * (size_t)PRE * sizeof(S);
+    static constexpr size_t bytes = off_bar + NSLOT * sizeof(unsigned long long);
 };
 
 template <int KIND, int LB, int MAXE, int MINB>
@@ -1212,9 +1215,9 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     C *s = reinterpret_cast<C *>(leaf_raw);
     S *pre = reinterpret_cast<S *>(leaf_raw + LY::off_pre);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(leaf_raw + LY::off_bar);
-    __shared__ LeafItem s_it[2];
-    __shared__ int64_t s_cs[2], s_ce[2];
-    __shared__ uint32_t s_ok[2];
+    __shared__ LeafItem s_it[LY::NSLOT];
+    __shared__ int64_t s_cs[LY::NSLOT], s_ce[LY::NSLOT];
+    __shared__ uint32_t s_ok[LY::NSLOT];
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
     // Leaf items queue up across levels (their ranges are never touched by a later
     // partition); a level's pass runs only when the queue would otherwise outgrow its
@@ -1252,16 +1255,15 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < LY::NSLOT; b++) mbar_init(&bar[b], 1);
         fence_mbar_init();
         claim(0);
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[LY::NSLOT] = {};
     uint64_t sorted = 0, filled = 0, items = 0;
     for (uint32_t iter = 0;; iter++) {
-        const int sl = (int)(iter & 1u);
+        const int sl = 0;                                 // the one prefetch slot
         if (!s_ok[sl]) break;
         const LeafItem it = s_it[sl];
         const int64_t cs = s_cs[sl], ce = s_ce[sl];
@@ -1292,7 +1294,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
         }
         fence_proxy_async();                // this slot's reads precede its next bulk copy
         __syncthreads();                    // sort buffer loaded, slot free, s_it read
-        if (threadIdx.x == 0) claim(sl ^ 1);            // prefetch the next item meanwhile
+        if (threadIdx.x == 0) claim(0);                   // prefetch the next item meanwhile
         if (is_fill) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
             S rep[V];
