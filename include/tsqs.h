@@ -66,9 +66,9 @@ typedef enum {
 typedef struct {
     int32_t  tile_items;       /* partition kernel shape, 0..3 (0 = default), given as
                                   consumer threads x keys per thread x staged tiles:
-                                  4-byte keys 192x32x3, 256x24x3, 256x32x3, 256x16x3;
-                                  8-byte keys 192x16x3, 256x12x3, 256x16x3, 256x8x3;
-                                  records     192x8x3,  256x6x3,  256x8x3,  256x4x3      */
+                                  4-byte keys 192x24x3, 192x32x3, 256x24x3, 256x16x3;
+                                  8-byte keys 192x12x3, 192x16x3, 256x12x3, 256x8x3;
+                                  records     192x6x3,  192x8x3,  256x6x3,  256x4x3      */
     int32_t  small_threshold;  /* segments of <= this many elements finish on chip,
                                   512..4096 (default 4096) for every key kind          */
     int32_t  ctas_per_sm;      /* resident CTAs per SM for the persistent kernels     */

@@ -26,9 +26,9 @@ KindOps make_ops() {
     o.pivot_block = kPivotBlock;
     o.leaf_smem = (int)LeafLayout<KIND>::bytes;
     o.leaf_max = kMaxSmall;
-    o.part[0] = part_variant<KIND, 192, 32, 3>();
-    o.part[1] = part_variant<KIND, 256, 24, 3>();
-    o.part[2] = part_variant<KIND, 256, 32, 3>();
+    o.part[0] = part_variant<KIND, 192, 24, 3>();
+    o.part[1] = part_variant<KIND, 192, 32, 3>();
+    o.part[2] = part_variant<KIND, 256, 24, 3>();
     o.part[3] = part_variant<KIND, 256, 16, 3>();
     o.k_init = (const void *)k_init<KIND>;
     o.k_orient = (const void *)k_orient<KIND>;

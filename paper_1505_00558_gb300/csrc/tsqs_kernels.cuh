@@ -718,7 +718,7 @@ struct PartLayout {
 // the 32-bit registers one thread's keys take (keys per thread x key size / 4).
 constexpr int part_min_blocks(int block, int words) {
     return words >= 32 ? (block >= 256 ? 2 : (block >= 192 ? 3 : 4))
-         : words >= 24 ? 3
+         : words >= 24 ? (block <= 192 ? 4 : 3)
          : (block >= 512 ? 2 : (block >= 256 ? 4 : 6));
 }
 
