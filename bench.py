@@ -42,9 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 # from an ncu capture of the kernel source with this sha256 prefix (null when the
 # kernel changed since).
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-width k_partition launch at the
-# headline size (2^27 int32, level 3 of an instrumented sort): 537.0 MB + 480.2 MB for
+# headline size (2^27 int32, level 3 of an instrumented sort): 537.0 MB + 480.1 MB for
 # 134,217,721 keys; valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"kernels_sha": "cd31b65f9bf709a1", "bytes_per_key": (537026304 + 480212224) / 134217721,
+NCU_TRAFFIC = {"kernels_sha": "5e4c54ec7615326d", "bytes_per_key": (537048832 + 480091904) / 134217721,
                "source": "profiles/k_partition_2e27_int32_traffic.md"}
 
 
