@@ -192,6 +192,30 @@ int tsqs_ctx_stats(tsqs_ctx *ctx, void *stream, tsqs_stats *out);   /* sync + re
 int tsqs_ctx_set_plan(tsqs_ctx *ctx, const tsqs_plan *plan);
 int tsqs_ctx_get_plan(const tsqs_ctx *ctx, tsqs_plan *out);
 
+/* ---------------------------------------------------------------------------------
+ * Streaming host arrays through the GPU (the paper's qsort() on host memory, applied
+ * to a sequence of independent arrays).
+ *   h_in[i]    host array of nmemb[i] elements of elem_size bytes (read only).
+ *   h_out[i]   host array that receives item i sorted ascending; it may be h_in[i]
+ *              (in place).  h_out == NULL sorts every item in place.
+ *   h_status   NULL, or a host array of count ints that receives each item's device
+ *              status (TSQS_OK, TSQS_ETIMEOUT, TSQS_EINTERNAL).
+ * Each item is copied to one of three device staging slots owned by the context, sorted
+ * there on `stream` (the items' sorts run one after another), and copied back.  The
+ * copies in and out run on two streams of the context's own, so while item i is sorted
+ * item i+1 is uploaded and item i-1 downloaded; with page-locked host arrays all three
+ * overlap, with pageable ones the copies are staged by the driver and overlap less.
+ * The staging slots (3 x the largest item's bytes) are kept until tsqs_ctx_destroy.
+ * Work queued on `stream` before the call is ordered before the first copy.  Returns
+ * after every item is in h_out: TSQS_OK, the first nonzero item status, TSQS_EINVAL
+ * (kind/size mismatch, an item of 2^31 or more elements, a NULL array for a non-empty
+ * item; nothing is queued), TSQS_ENOMEM (staging or scratch could not be allocated;
+ * nothing is queued) or TSQS_ECUDA.  Arrays of 0 or 1 element are copied unchanged.
+ * ------------------------------------------------------------------------------- */
+int tsqs_ctx_sort_host_stream(tsqs_ctx *ctx, const void *const *h_in, void *const *h_out,
+                              const size_t *nmemb, size_t count, size_t elem_size,
+                              int key_kind, void *stream, int *h_status);
+
 /* Bytes of device scratch a context needs for a sort of this shape. */
 size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
                               const tsqs_plan *plan);

@@ -170,6 +170,35 @@ class Context:
     def set_plan(self, plan: Plan):
         _check(lib().tsqs_ctx_set_plan(self.handle, ctypes.byref(plan)), "tsqs_ctx_set_plan")
 
+    def sort_host_stream(self, ins, outs=None, *, kind: int | None = None, records: bool = False,
+                         stream=None) -> list:
+        """Sorts a sequence of contiguous CPU tensors through the GPU with uploads and
+        downloads overlapping the sorts (tsqs_ctx_sort_host_stream).  ``outs`` None sorts
+        in place; otherwise outs[i] (same size as ins[i]) receives ins[i] sorted.
+        Returns each item's device status; raises on a nonzero return."""
+        ins = list(ins)
+        outs = ins if outs is None else list(outs)
+        if len(outs) != len(ins):
+            raise ValueError("ins and outs differ in length")
+        kind = kind or (key_kind_of(ins[0], records) if ins else TSQS_I32)
+        es = ELEM_SIZE[kind]
+        cnt = len(ins)
+        p_in = (ctypes.c_void_p * max(1, cnt))()
+        p_out = (ctypes.c_void_p * max(1, cnt))()
+        sizes = (ctypes.c_size_t * max(1, cnt))()
+        for i, (a, b) in enumerate(zip(ins, outs)):
+            if a.is_cuda or b.is_cuda or not a.is_contiguous() or not b.is_contiguous():
+                raise ValueError("expected contiguous CPU tensors")
+            nb = a.numel() * a.element_size()
+            if b.numel() * b.element_size() != nb:
+                raise ValueError("input and output sizes differ")
+            p_in[i], p_out[i], sizes[i] = a.data_ptr(), b.data_ptr(), nb // es
+        st = (ctypes.c_int * max(1, cnt))()
+        rc = lib().tsqs_ctx_sort_host_stream(self.handle, p_in, p_out, sizes, cnt, es, kind,
+                                             ctypes.c_void_p(_stream_handle(stream)), st)
+        _check(rc, "tsqs_ctx_sort_host_stream")
+        return [st[i] for i in range(cnt)]
+
     def sort_timed(self, t, *, kind: int | None = None, records: bool = False, stream=None,
                    max_levels: int = 256):
         """Level-by-level run of the same kernels with CUDA events around each

@@ -72,6 +72,7 @@ SIGNATURES = {
     "tsqs_ctx_stats": (_i, [_vp, _vp, ctypes.POINTER(Stats)]),
     "tsqs_ctx_set_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tsqs_ctx_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
+    "tsqs_ctx_sort_host_stream": (_i, [_vp, _vp, _vp, _vp, _sz, _sz, _i, _vp, _vp]),
     "tsqs_scratch_bytes_for": (_sz, [_sz, _sz, _sz, ctypes.POINTER(Plan)]),
     "tsqs_plan_default": (_i, [_i, _sz, ctypes.POINTER(Plan)]),
     "tsqs_ctx_sort_timed": (_i, [_vp, _vp, _sz, _sz, _i, _vp, ctypes.POINTER(ctypes.c_float),

@@ -9,6 +9,11 @@ __global__ void k_setup(Job *job, Ctl *ctl, Job j) {
     for (uint32_t i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) c[i] = 0u;
 }
 
+// Keeps one sort's device status (0 when no sort ran for the item) in a per-item word.
+__global__ void k_keep_status(const Ctl *ctl, uint32_t *dst, int ran) {
+    if (threadIdx.x == 0) *dst = ran ? ctl->status : 0u;
+}
+
 __global__ void k_dbg_counts(const Job *__restrict__ job, Ctl *) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < job->nseg;
          s += (uint64_t)gridDim.x * blockDim.x) {

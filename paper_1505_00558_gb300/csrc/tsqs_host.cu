@@ -26,6 +26,7 @@ using namespace tsqs;
 
 namespace tsqs {
 __global__ void k_setup(Job *job, Ctl *ctl, Job j);
+__global__ void k_keep_status(const Ctl *ctl, uint32_t *dst, int ran);
 }
 bool tsqs_cached_plan(int kind, size_t n, size_t nseg, tsqs_plan *out);
 
@@ -152,6 +153,13 @@ struct tsqs_ctx {
     size_t wide_rec_bytes = 0;
     char *wide_tmp = nullptr;          // large elements: the gathered copy
     size_t wide_tmp_bytes = 0;
+    // host-array streaming: device staging slots, the two copy streams, their events
+    char *stage[3] = {};
+    size_t stage_bytes = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_in[3] = {}, ev_sorted[3] = {}, ev_out[3] = {};
+    uint32_t *d_item_status = nullptr;
+    size_t item_status_cap = 0;
     std::recursive_mutex mu;
 };
 
@@ -474,6 +482,49 @@ int read_status(tsqs_ctx *c, cudaStream_t stream, bool clear) {
     return (int)st;
 }
 
+int ctx_stream_setup(tsqs_ctx *c, size_t slot_bytes, size_t count) {
+    if (!c->s_in) {
+        CK(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+        for (int k = 0; k < 3; k++) {
+            CK(cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->ev_sorted[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming));
+        }
+    }
+    // every call ends with its streams drained, so the slots are idle here
+    if (slot_bytes > c->stage_bytes) {
+        for (int k = 0; k < 3; k++) {
+            if (c->stage[k]) cudaFree(c->stage[k]);
+            c->stage[k] = nullptr;
+        }
+        c->stage_bytes = 0;
+        for (int k = 0; k < 3; k++) {
+            if (cudaMalloc((void **)&c->stage[k], slot_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                for (int q = 0; q <= k; q++) {
+                    if (c->stage[q]) cudaFree(c->stage[q]);
+                    c->stage[q] = nullptr;
+                }
+                return TSQS_ENOMEM;
+            }
+        }
+        c->stage_bytes = slot_bytes;
+    }
+    if (count > c->item_status_cap) {
+        if (c->d_item_status) cudaFree(c->d_item_status);
+        c->d_item_status = nullptr;
+        c->item_status_cap = 0;
+        if (cudaMalloc((void **)&c->d_item_status, count * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return TSQS_ENOMEM;
+        }
+        c->item_status_cap = count;
+    }
+    return TSQS_OK;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -503,6 +554,16 @@ void tsqs_ctx_destroy(tsqs_ctx *c) {
         if (c->scratch) cudaFree(c->scratch);
         if (c->wide_rec) cudaFree(c->wide_rec);
         if (c->wide_tmp) cudaFree(c->wide_tmp);
+        for (int k = 0; k < 3; k++) {
+            if (c->stage[k]) cudaFree(c->stage[k]);
+            if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+            if (c->ev_sorted[k]) cudaEventDestroy(c->ev_sorted[k]);
+            if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+        }
+        if (c->ev_entry) cudaEventDestroy(c->ev_entry);
+        if (c->s_in) cudaStreamDestroy(c->s_in);
+        if (c->s_out) cudaStreamDestroy(c->s_out);
+        if (c->d_item_status) cudaFree(c->d_item_status);
         if (c->d_job) cudaFree(c->d_job);
         if (c->d_ctl) cudaFree(c->d_ctl);
         if (c->done_ev) cudaEventDestroy(c->done_ev);
@@ -734,6 +795,81 @@ int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, v
     }
     CK(cudaStreamSynchronize(s));
     return TSQS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Host arrays streamed through three device staging slots: item i's upload runs on
+// s_in, its sort on the caller's stream, its download on s_out.  Slot i % 3 is reused
+// by item i + 3 once item i's download has finished (ev_out), so the upload of item
+// i + 1 and the download of item i - 1 overlap the sort of item i.
+// ---------------------------------------------------------------------------------
+
+int tsqs_ctx_sort_host_stream(tsqs_ctx *c, const void *const *h_in, void *const *h_out,
+                              const size_t *nmemb, size_t count, size_t elem_size,
+                              int key_kind, void *stream, int *h_status) {
+    if (!c) return TSQS_EINVAL;
+    const size_t es = kind_size(key_kind);
+    if (!es || es != elem_size) return TSQS_EINVAL;
+    if (count == 0) return TSQS_OK;
+    if (!h_in || !nmemb) return TSQS_EINVAL;
+    size_t max_n = 0;
+    for (size_t i = 0; i < count; i++) {
+        if (nmemb[i] >= (1ull << 31)) return TSQS_EINVAL;
+        const void *out = h_out ? h_out[i] : h_in[i];
+        if (nmemb[i] > 0 && (!h_in[i] || !out)) return TSQS_EINVAL;
+        max_n = std::max(max_n, nmemb[i]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const KindOps *o = get_ops(key_kind);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    int rc = ctx_init_device(c);
+    if (rc) return rc;
+    if ((rc = ctx_kind_setup(c, o))) return rc;
+    // everything that can fail to allocate is allocated before anything is queued
+    const size_t slot_bytes = std::max<size_t>(max_n * es, 16);
+    if ((rc = ctx_stream_setup(c, slot_bytes, count))) return rc;
+    if (max_n > 1) {
+        if ((rc = ctx_ensure_scratch(c, max_n, 1, es, part_of(o, c->plan).tile, o->leaf_max))) return rc;
+        if ((rc = ctx_build_graph(c, o))) return rc;
+    }
+    int first = TSQS_OK;
+    CK(cudaEventRecord(c->ev_entry, s));
+    CK(cudaStreamWaitEvent(c->s_in, c->ev_entry, 0));
+    CK(cudaStreamWaitEvent(c->s_out, c->ev_entry, 0));
+    for (size_t i = 0; i < count && first == TSQS_OK; i++) {
+        const int k = (int)(i % 3);
+        const size_t n = nmemb[i], bytes = n * es;
+        void *out = h_out ? h_out[i] : const_cast<void *>(h_in[i]);
+        if (i >= 3 && cudaStreamWaitEvent(c->s_in, c->ev_out[k], 0) != cudaSuccess) { first = TSQS_ECUDA; break; }
+        if (bytes && cudaMemcpyAsync(c->stage[k], h_in[i], bytes, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess) { first = TSQS_ECUDA; break; }
+        if (cudaEventRecord(c->ev_in[k], c->s_in) != cudaSuccess ||
+            cudaStreamWaitEvent(s, c->ev_in[k], 0) != cudaSuccess) { first = TSQS_ECUDA; break; }
+        if (n > 1 && (first = ctx_launch(c, c->stage[k], n, nullptr, 0, es, key_kind, s)) != TSQS_OK) break;
+        k_keep_status<<<1, 32, 0, s>>>(c->d_ctl, c->d_item_status + i, n > 1 ? 1 : 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaEventRecord(c->ev_sorted[k], s) != cudaSuccess ||
+            cudaStreamWaitEvent(c->s_out, c->ev_sorted[k], 0) != cudaSuccess) { first = TSQS_ECUDA; break; }
+        if (bytes && cudaMemcpyAsync(out, c->stage[k], bytes, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess) { first = TSQS_ECUDA; break; }
+        if (cudaEventRecord(c->ev_out[k], c->s_out) != cudaSuccess) { first = TSQS_ECUDA; break; }
+    }
+    // drain all three streams whatever happened, so the slots are idle for the next call
+    const cudaError_t e_in = cudaStreamSynchronize(c->s_in);
+    const cudaError_t e_s = cudaStreamSynchronize(s);
+    const cudaError_t e_out = cudaStreamSynchronize(c->s_out);
+    if (first != TSQS_OK) return first;
+    if (e_in != cudaSuccess || e_s != cudaSuccess || e_out != cudaSuccess) return TSQS_ECUDA;
+    uint32_t *st = (uint32_t *)malloc(count * sizeof(uint32_t));
+    if (!st) return TSQS_ENOMEM;
+    if (cudaMemcpy(st, c->d_item_status, count * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        free(st);
+        return TSQS_ECUDA;
+    }
+    for (size_t i = 0; i < count; i++) {
+        if (h_status) h_status[i] = (int)st[i];
+        if (first == TSQS_OK && st[i]) first = (int)st[i];
+    }
+    free(st);
+    return first;
 }
 
 // ---------------------------------------------------------------------------------
