@@ -865,17 +865,30 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
                     if (c_lt(pd, d)) gtm |= 1u << i;
                 }
             } else if (covered) {                        // segment ends inside the tile
-#pragma unroll
-                for (int k = 0; k < NV; k++) lds_vec<S, V>(buf + (k * BLOCK + tid) * V, &v[k * V]);
+                // range tests per 16-byte vector: a vector wholly outside [lo, hi) is
+                // neither loaded nor classified (no bits; staging sends it to the dummy
+                // slot), one wholly inside takes the unchecked compares, and only the
+                // vectors holding lo or hi test every element
 #pragma unroll
                 for (int k = 0; k < NV; k++) {
+                    const int vs = (k * BLOCK + tid) * V;
+                    if (vs + V <= lo || vs >= hi) continue;
+                    lds_vec<S, V>(buf + vs, &v[k * V]);
+                    if (vs >= lo && vs + V <= hi) {
 #pragma unroll
-                    for (int j = 0; j < V; j++) {
-                        const int idx = (k * BLOCK + tid) * V + j;
-                        const bool in = idx >= lo && idx < hi;
-                        const D d = K::dom(v[k * V + j]);
-                        ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
-                        gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
+                        for (int j = 0; j < V; j++) {
+                            const D d = K::dom(v[k * V + j]);
+                            if (c_lt(d, pd)) ltm |= 1u << (k * V + j);
+                            if (c_lt(pd, d)) gtm |= 1u << (k * V + j);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < V; j++) {
+                            const bool in = vs + j >= lo && vs + j < hi;
+                            const D d = K::dom(v[k * V + j]);
+                            ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
+                            gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
+                        }
                     }
                 }
             } else {                                     // the buffer's own ends
