@@ -699,6 +699,44 @@ struct TileMeta {
     uint32_t tile, si, tl, ntiles_seg, tile_begin, valid;
 };
 
+// Producer: claims tile `it` of this CTA (two tiles per atomic in atomic mode, one in
+// look-back mode) and fills its TileMeta from the tile table and the segment descriptor.
+template <int TILE, int V>
+__device__ __forceinline__ void producer_meta(const Job *job, Ctl *ctl, int par, uint32_t it,
+                                              uint32_t &claim, uint32_t ntiles, uint32_t nfront,
+                                              int64_t e_lo, int64_t e_hi, TileMeta &m) {
+    if (job->offset_mode != 0u) {
+        m.tile = atomicAdd(&ctl->tile_claim, 1u);
+    } else {
+        if ((it & 1u) == 0u) claim = atomicAdd(&ctl->tile_claim, 2u);
+        m.tile = claim + (it & 1u);
+    }
+    m.valid = 0;
+    m.cs = m.ce = 0;
+    if (m.tile < ntiles) {
+        m.si = job->tile_seg[m.tile];
+        if (m.si < nfront) {
+            const SegDesc sd = job->front[par][m.si];
+            m.valid = 1;
+            m.sb = sd.begin; m.se = sd.end;
+            m.piv_lo = sd.piv_lo; m.piv_hi = sd.piv_hi;
+            m.tile_begin = sd.tile_begin; m.ntiles_seg = sd.ntiles;
+            m.tl = m.tile - sd.tile_begin;
+            m.t0 = sd.s0 + (int64_t)m.tl * TILE;
+            // aligned hull of the segment inside the tile, clipped to the buffer
+            const int64_t a_sb = (int64_t)sd.begin - (((int64_t)sd.begin + job->vec_off) % V);
+            const int64_t a_se = (int64_t)sd.end + ((V - (((int64_t)sd.end + job->vec_off) % V)) % V);
+            m.cs = max(max(m.t0, a_sb), e_lo);
+            m.ce = min(min(m.t0 + TILE, a_se), e_hi);
+            if (m.ce < m.cs) m.ce = m.cs;
+        } else {
+            set_status(ctl, TSQS_EINTERNAL);
+        }
+    } else {
+        m.tile = 0xFFFFFFFFu;                      // end of work
+    }
+}
+
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
 struct PartLayout {
     using S = typename Key<KIND>::S;
@@ -768,46 +806,19 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
         const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
         const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
         uint32_t claim = 0;
+        const bool lookback_mode = job->offset_mode != 0u;
+        TileMeta m;
         for (uint32_t it = 0;; it++) {
             const int s = (int)(it % NBUF);
+            // atomic mode: tile it's claim and descriptor were read before the wait below
+            // (at the end of the previous iteration), so their latency overlaps the wait
+            // for the slot.  Look-back mode: a claimed tile must start at once (its
+            // successors wait for its aggregate), so it is claimed after the wait.
+            if (it == 0u && !lookback_mode) producer_meta<TILE, V>(job, ctl, par, it, claim, ntiles, nfront, e_lo, e_hi, m);
             if (it >= (uint32_t)NBUF && !mbar_wait(&empty[s], ((it / NBUF) - 1) & 1u, wait_limit)) {
                 set_status(ctl, TSQS_ETIMEOUT);
             }
-            TileMeta m;
-            // tiles are claimed two at a time (one atomic per pair); the pair's second
-            // tile is used on the next slot
-            if (job->offset_mode != 0u) {
-                // look-back mode: a claimed tile must start at once (its successors wait
-                // for its aggregate), so claim one at a time
-                m.tile = atomicAdd(&ctl->tile_claim, 1u);
-            } else {
-                if ((it & 1u) == 0u) claim = atomicAdd(&ctl->tile_claim, 2u);
-                m.tile = claim + (it & 1u);
-            }
-            m.valid = 0;
-            m.cs = m.ce = 0;
-            if (m.tile < ntiles) {
-                m.si = job->tile_seg[m.tile];
-                if (m.si < nfront) {
-                    const SegDesc sd = job->front[par][m.si];
-                    m.valid = 1;
-                    m.sb = sd.begin; m.se = sd.end;
-                    m.piv_lo = sd.piv_lo; m.piv_hi = sd.piv_hi;
-                    m.tile_begin = sd.tile_begin; m.ntiles_seg = sd.ntiles;
-                    m.tl = m.tile - sd.tile_begin;
-                    m.t0 = sd.s0 + (int64_t)m.tl * TILE;
-                    // aligned hull of the segment inside the tile, clipped to the buffer
-                    const int64_t a_sb = (int64_t)sd.begin - (((int64_t)sd.begin + job->vec_off) % V);
-                    const int64_t a_se = (int64_t)sd.end + ((V - (((int64_t)sd.end + job->vec_off) % V)) % V);
-                    m.cs = max(max(m.t0, a_sb), e_lo);
-                    m.ce = min(min(m.t0 + TILE, a_se), e_hi);
-                    if (m.ce < m.cs) m.ce = m.cs;
-                } else {
-                    set_status(ctl, TSQS_EINTERNAL);
-                }
-            } else {
-                m.tile = 0xFFFFFFFFu;                      // end of work
-            }
+            if (lookback_mode) producer_meta<TILE, V>(job, ctl, par, it, claim, ntiles, nfront, e_lo, e_hi, m);
             meta[s] = m;
             if (m.valid && m.ce > m.cs) {
                 const uint32_t bytes = (uint32_t)((m.ce - m.cs) * (int64_t)sizeof(S));
@@ -817,6 +828,7 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
                 mbar_arrive(&full[s]);
             }
             if (m.tile == 0xFFFFFFFFu) break;
+            if (!lookback_mode) producer_meta<TILE, V>(job, ctl, par, it + 1, claim, ntiles, nfront, e_lo, e_hi, m);
         }
         return;
     }
