@@ -493,46 +493,74 @@ __device__ typename K::C sample_pivot(const typename K::S *src, uint64_t b, uint
     if ((uint64_t)S > m) S = (uint32_t)m;
     if ((S & 1u) == 0) S -= 1;                       // odd: one true median
     if (S == 0) S = 1;
+    // stratum k is [b + floor(m k / S), b + floor(m (k+1) / S)); with m = q S + r,
+    // floor(m k / S) = q k + floor(r k / S), and r k < 63 * 64, so below 2^32 elements
+    // every division is a 32-bit one
+    const bool narrow = m < (1ull << 32);
+    const uint32_t q = narrow ? (uint32_t)m / S : 0u, r = narrow ? (uint32_t)m % S : 0u;
     C v[2];
-    bool ok[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const uint32_t k = (uint32_t)lane + 32u * h;
-        ok[h] = k < S;
         v[h] = c_max<C>();
-        if (ok[h]) {
-            const uint64_t lo = b + (m * k) / S, hi = b + (m * (k + 1)) / S;
+        if (k < S) {
+            uint64_t lo, w;
+            if (narrow) {
+                const uint32_t a0 = q * k + (r * k) / S, a1 = q * (k + 1) + (r * (k + 1)) / S;
+                lo = b + a0;
+                w = a1 - a0;
+            } else {
+                lo = b + (m * k) / S;
+                w = b + (m * (k + 1)) / S - lo;
+            }
             const uint64_t z = mix64(seed ^ (b * 0x9E3779B97F4A7C15ull) ^ (e * 0xC2B2AE3D27D4EB4Full)
                                      ^ ((uint64_t)(k + 1) * 0x165667B19E3779F9ull));
-            const uint64_t pos = lo + (hi > lo ? z % (hi - lo) : 0);
+            // offset in [0, w): below 2^32 elements the high word of z times w, shifted
+            // down (Lemire's multiply-shift range reduction), else z mod w
+            const uint64_t pos = lo + (narrow ? (((z >> 32) * w) >> 32) : z % w);
             if (positions) positions[k] = pos;
             v[h] = K::canon(src[pos]);
         }
     }
-    // rank of each sample: #smaller + #equal with a lower index (ties broken by index)
-    uint32_t rank[2] = {0, 0};
-    for (int sl = 0; sl < 32; sl++) {
+    // the median is the sample of rank (S - 1) / 2: sort the samples across the warp
+    // with a bitonic network (unused entries hold the largest key, so they sort last)
+    const uint32_t want = (S - 1) / 2;
+    if (S <= 32u) {
+        // one sample per lane, element index = lane
+        C x = v[0];
 #pragma unroll
-        for (int g = 0; g < 2; g++) {
-            const C y = c_shfl(v[g], sl);
-            const uint32_t ky = (uint32_t)sl + 32u * g;
-            if (ky < S) {
+        for (uint32_t k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const uint32_t k = (uint32_t)lane + 32u * h;
-                    rank[h] += (c_lt(y, v[h]) || (c_eq(y, v[h]) && ky < k)) ? 1u : 0u;
-                }
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const C y = c_shfl(x, lane ^ (int)j);
+                const bool keep_min = (((uint32_t)lane & k) == 0u) == (((uint32_t)lane & j) == 0u);
+                if (keep_min ? c_lt(y, x) : c_lt(x, y)) x = y;
             }
         }
+        return c_shfl(x, (int)want);
     }
-    const uint32_t want = (S - 1) / 2;
-    C piv = v[0];
+    // two samples per lane: element 2 lane + h holds the sample drawn as lane + 32 h
+    // (the assignment of samples to elements does not change their order statistics)
+    C x0 = v[0], x1 = v[1];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const unsigned hit = __ballot_sync(0xffffffffu, ok[h] && rank[h] == want);
-        if (hit) piv = c_shfl(v[h], __ffs(hit) - 1);
+    for (uint32_t k = 2; k <= 64; k <<= 1) {
+        const bool asc = ((2u * (uint32_t)lane) & k) == 0u;
+#pragma unroll
+        for (uint32_t j = k >> 1; j > 1; j >>= 1) {
+            const C y0 = c_shfl(x0, lane ^ (int)(j >> 1));
+            const C y1 = c_shfl(x1, lane ^ (int)(j >> 1));
+            const bool keep_min = asc == (((2u * (uint32_t)lane) & j) == 0u);
+            if (keep_min ? c_lt(y0, x0) : c_lt(x0, y0)) x0 = y0;
+            if (keep_min ? c_lt(y1, x1) : c_lt(x1, y1)) x1 = y1;
+        }
+        // stride 1: the lane's own pair
+        const bool sw = asc ? c_lt(x1, x0) : c_lt(x0, x1);
+        const C t = x0;
+        x0 = sw ? x1 : x0;
+        x1 = sw ? t : x1;
     }
-    return piv;
+    const C m0 = c_shfl(x0, (int)(want >> 1)), m1 = c_shfl(x1, (int)(want >> 1));
+    return (want & 1u) ? m1 : m0;
 }
 
 // One warp per frontier segment (grid-stride over warps): the sampled median, then the
