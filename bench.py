@@ -335,15 +335,15 @@ def gpu_arm(args, dist):
     value = keys_all / (total_ms * 1e-3) / 1e6
     ms_step = total_ms / K
 
-    # launches per sort: setup, the three presortedness kernels, init, 4 per level
-    # iteration (leaf, pivot, partition, level end), the final leaf pass and the depth
-    # guard's prep, tile and finish kernels (its stage loop runs no iteration here)
+    # launches per sort: setup, the three presortedness kernels, init, 3 per level
+    # iteration (pivot, partition, level end), the leaf pass and the loop control after
+    # the levels (the depth guard's branch is skipped: no segment reaches its level)
     ctx = T.Context()
     chk = src.clone()
     T.sort_(chk, kind=T.TSQS_I32, ctx=ctx)
     st = ctx.stats()
     iters = max(1, st["levels"])
-    launches_per_sort = 9 + 4 * iters
+    launches_per_sort = 7 + 3 * iters
     del copies
 
     # dominant kernel: partition levels, timed one launch at a time with CUDA events

@@ -274,6 +274,14 @@ void tsqs_debug_set_spin_limit(uint32_t polls);
  * value to run the fallback on ordinary inputs. */
 void tsqs_debug_set_deep_level(uint32_t level);
 
+/* Caps, for sorts that start afterwards (every context), how many leaf items may wait
+ * in the queue before the level loop pauses for a leaf pass.  By default the queue holds
+ * two levels' worth of items and the loop pauses once more than one level's worth is
+ * waiting, which ordinary inputs never reach, so all leaves are sorted in one pass after
+ * the last level.  Tests set a small value to run the pause-and-resume path of the level
+ * loop on ordinary inputs.  0 restores the default. */
+void tsqs_debug_set_leaf_defer(uint32_t items);
+
 /* When on != 0, partition tile 1 of every later level of the default context never
  * publishes its look-back word, so the waits of its successors must run into the
  * spin limit and the sort must end with TSQS_ETIMEOUT (a host-side fault injection

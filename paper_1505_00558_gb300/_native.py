@@ -83,6 +83,7 @@ SIGNATURES = {
     "tsqs_debug_small_sort": (_i, [_vp, _sz, _sz, _i, _vp, _sz, _vp]),
     "tsqs_debug_set_spin_limit": (None, [_u32]),
     "tsqs_debug_set_deep_level": (None, [_u32]),
+    "tsqs_debug_set_leaf_defer": (None, [_u32]),
     "tsqs_debug_withhold_publish": (None, [_i]),
     "tsqs_plan_autotune": (_i, [_i, _sz, _sz, _vp, ctypes.POINTER(Plan)]),
     "tsqs_plan_cache_save": (_i, [ctypes.c_char_p]),

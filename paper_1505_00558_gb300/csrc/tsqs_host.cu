@@ -27,6 +27,8 @@ using namespace tsqs;
 namespace tsqs {
 __global__ void k_setup(Job *job, Ctl *ctl, Job j);
 __global__ void k_keep_status(const Ctl *ctl, uint32_t *dst, int ran);
+__global__ void k_outer_control(const Ctl *ctl, cudaGraphConditionalHandle h_levels,
+                                cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_deep);
 }
 bool tsqs_cached_plan(int kind, size_t n, size_t nseg, tsqs_plan *out);
 
@@ -130,6 +132,7 @@ void normalise_plan(tsqs_plan *p) {
 
 uint32_t g_debug_spin = 0;        // 0 = default
 uint32_t g_debug_deep = 0;        // depth-guard level; 0 = default (2 log2 n + 8)
+uint32_t g_debug_defer = 0;       // leaf-queue pause threshold; 0 = default (one level's worth)
 int g_debug_withhold = 0;
 
 }  // namespace
@@ -266,7 +269,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
-    j->leaf_defer = L.leaf_defer;
+    j->leaf_defer = g_debug_defer ? std::min(g_debug_defer, L.leaf_defer) : L.leaf_defer;
     j->small_T = (uint32_t)eff_threshold(c->plan, o->leaf_max);
     j->samples = (uint32_t)c->plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));
@@ -309,34 +312,40 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.gridDim = dim3(c->sms * 2);
     CK(cudaGraphAddKernelNode(&n_init, g, &n_pre, 1, &kp));
 
+    // outer loop: { level loop ; leaf pass ; control }.  The level loop pauses only when
+    // the leaf queue could not take another level's items; normally the outer body runs
+    // once and its leaf pass is the single one after all levels.
+    cudaGraphConditionalHandle h_out;
+    CK(cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cpo{};
+    cpo.type = cudaGraphNodeTypeConditional;
+    cpo.conditional.handle = h_out;
+    cpo.conditional.type = cudaGraphCondTypeWhile;
+    cpo.conditional.size = 1;
+    cudaGraphNode_t n_outer;
+    CK(cudaGraphAddNode(&n_outer, g, &n_init, nullptr, 1, &cpo));
+    cudaGraph_t outer = cpo.conditional.phGraph_out[0];
+
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t n_loop;
-    CK(cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp));
+    CK(cudaGraphAddNode(&n_loop, outer, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
-    cudaGraphNode_t n_leaf, n_piv, n_part, n_fin, n_last;
-    int leaf_final = 0, leaf_last = 1;
-    void *argsl[] = {&pj, &pc, &leaf_final};
+    cudaGraphNode_t n_piv, n_part, n_fin, n_last, n_octl;
+    int leaf_last = 1;
     void *argsl_last[] = {&pj, &pc, &leaf_last};
-    kp = cudaKernelNodeParams{};
-    kp.func = (void *)o->k_leaf;
-    kp.gridDim = dim3(c->leaf_grid[k]);
-    kp.blockDim = dim3(o->leaf_block);
-    kp.sharedMemBytes = (unsigned)o->leaf_smem;
-    kp.kernelParams = argsl;
-    CK(cudaGraphAddKernelNode(&n_leaf, body, nullptr, 0, &kp));
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_pivot;
     kp.gridDim = dim3(c->sms * 4);
     kp.blockDim = dim3(o->pivot_block);
     kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_piv, body, &n_leaf, 1, &kp));
+    CK(cudaGraphAddKernelNode(&n_piv, body, nullptr, 0, &kp));
     kp = cudaKernelNodeParams{};
     const PartVariant &pv = part_of(o, c->plan);
     kp.func = (void *)pv.k_partition;
@@ -354,17 +363,37 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.blockDim = dim3(128);
     kp.kernelParams = argsf;
     CK(cudaGraphAddKernelNode(&n_fin, body, &n_part, 1, &kp));
-    // the final leaf pass, after the loop
+    // the leaf pass after the level loop: every queued item, then the queue is empty
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_leaf;
     kp.gridDim = dim3(c->leaf_grid[k]);
     kp.blockDim = dim3(o->leaf_block);
     kp.sharedMemBytes = (unsigned)o->leaf_smem;
     kp.kernelParams = argsl_last;
-    CK(cudaGraphAddKernelNode(&n_last, g, &n_loop, 1, &kp));
-    // depth guard, beside the final leaf pass: prep, tile sorts, a WHILE over the stages
+    CK(cudaGraphAddKernelNode(&n_last, outer, &n_loop, 1, &kp));
+    // the depth guard's branch after the loops, under an IF node set by the control
+    cudaGraphConditionalHandle h_if;
+    CK(cudaGraphConditionalHandleCreate(&h_if, g, 0, cudaGraphCondAssignDefault));
+    const Ctl *pcc = pc;
+    void *argso[] = {&pcc, &h, &h_out, &h_if};
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)k_outer_control;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = argso;
+    CK(cudaGraphAddKernelNode(&n_octl, outer, &n_last, 1, &kp));
+    // depth guard (IF some segment reached the bound): prep, tile sorts, a WHILE over
+    // the stages, finish
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_if;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t n_if;
+    CK(cudaGraphAddNode(&n_if, g, &n_outer, nullptr, 1, &ip));
+    cudaGraph_t dg = ip.conditional.phGraph_out[0];
     cudaGraphConditionalHandle hd;
-    CK(cudaGraphConditionalHandleCreate(&hd, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&hd, dg, 0, cudaGraphCondAssignDefault));
     int use_hd = 1;
     void *argsd[] = {&pj, &pc, &hd, &use_hd};
     cudaGraphNode_t n_dprep, n_dtiles, n_dloop, n_dstage, n_dfin;
@@ -373,20 +402,20 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(512);
     kp.kernelParams = argsd;
-    CK(cudaGraphAddKernelNode(&n_dprep, g, &n_loop, 1, &kp));
+    CK(cudaGraphAddKernelNode(&n_dprep, dg, nullptr, 0, &kp));
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_deep_tiles;
     kp.gridDim = dim3(c->sms * 2);
     kp.blockDim = dim3(512);
     kp.sharedMemBytes = (unsigned)o->deep_smem;
     kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_dtiles, g, &n_dprep, 1, &kp));
+    CK(cudaGraphAddKernelNode(&n_dtiles, dg, &n_dprep, 1, &kp));
     cudaGraphNodeParams dp{};
     dp.type = cudaGraphNodeTypeConditional;
     dp.conditional.handle = hd;
     dp.conditional.type = cudaGraphCondTypeWhile;
     dp.conditional.size = 1;
-    CK(cudaGraphAddNode(&n_dloop, g, &n_dtiles, nullptr, 1, &dp));
+    CK(cudaGraphAddNode(&n_dloop, dg, &n_dtiles, nullptr, 1, &dp));
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_deep_stage;
     kp.gridDim = dim3(c->sms * 2);
@@ -399,7 +428,7 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.gridDim = dim3(c->sms * 2);
     kp.blockDim = dim3(512);
     kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_dfin, g, &n_dloop, 1, &kp));
+    CK(cudaGraphAddKernelNode(&n_dfin, dg, &n_dloop, 1, &kp));
 
     cudaGraphExec_t ex = nullptr;
     CK(cudaGraphInstantiate(&ex, g, 0));
@@ -748,6 +777,7 @@ int tsqs_sort_wide(void *base, size_t nmemb, size_t elem_size, size_t key_offset
 
 void tsqs_debug_set_spin_limit(uint32_t polls) { g_debug_spin = polls; }
 void tsqs_debug_set_deep_level(uint32_t level) { g_debug_deep = level; }
+void tsqs_debug_set_leaf_defer(uint32_t items) { g_debug_defer = items; }
 void tsqs_debug_withhold_publish(int on) { g_debug_withhold = on ? 1 : 0; }
 
 // ---------------------------------------------------------------------------------
@@ -925,7 +955,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
                             (size_t)pv.smem, s));
         CK(cudaEventRecord(ev[1], s));
         CK(cudaLaunchKernel(o->k_finish, dim3(c->sms), dim3(128), argsf, 0, s));
-        CK(cudaMemcpyAsync(c->h_cont, &c->d_ctl->cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->h_cont, &c->d_ctl->more, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (L < max_levels) {
             float ms = 0.f, lms = 0.f;
@@ -1113,7 +1143,7 @@ int host_make_job_at(const KindOps *o, const tsqs_plan &plan, void *base, size_t
     j->cap_front = L.cap_front;
     j->cap_tiles = L.cap_tiles;
     j->cap_leaves = L.cap_leaves;
-    j->leaf_defer = L.leaf_defer;
+    j->leaf_defer = g_debug_defer ? std::min(g_debug_defer, L.leaf_defer) : L.leaf_defer;
     j->small_T = (uint32_t)eff_threshold(plan, o->leaf_max);
     j->samples = (uint32_t)plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));

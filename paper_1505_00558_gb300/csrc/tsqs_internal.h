@@ -50,7 +50,7 @@ struct Ctl {
     uint32_t tile_claim;      // partition tiles claimed in this level
     uint32_t leaf_claim;      // leaf items claimed by the running leaf pass
     uint32_t seg_claim;       // frontier segments claimed by the pivot kernel
-    uint32_t cont;            // level loop continues (host-driven mode reads it)
+    uint32_t cont;            // the level loop runs another level now (graph: inner loop)
     uint32_t nfront[2];
     uint32_t ntiles[2];
     uint32_t nleaf;           // leaf items queued (across levels, until a leaf pass)
@@ -64,7 +64,8 @@ struct Ctl {
     uint32_t max_front;
     uint32_t levels_done;
     uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
-    uint32_t pad_;
+    uint32_t more;            // levels remain (after a leaf pass if cont is 0); host-driven
+                              // mode reads it
     uint64_t front_keys[2];
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;

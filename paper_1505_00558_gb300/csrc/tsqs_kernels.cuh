@@ -1678,7 +1678,9 @@ __global__ void k_deep_finish(const Job *__restrict__ job, Ctl *ctl) {
 }
 
 // Level control (one thread).  Records the level's statistics, resets the consumed
-// queues, advances the level and sets the loop condition.
+// queues, advances the level and sets the loop condition: `more` when the next level's
+// frontier is not empty, `cont` (the graph's level loop) only while the leaf queue also
+// has room for another level's items; otherwise the loop pauses for a leaf pass.
 __device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGraphConditionalHandle handle,
                               int use_handle) {
     const uint32_t L = ctl->level;
@@ -1695,7 +1697,9 @@ __device__ __forceinline__ void level_control(const Job *job, Ctl *ctl, cudaGrap
     ctl->level = L + 1;
     const bool more = ctl->nfront[par ^ 1] != 0u;    // queued leaves wait for a leaf pass
     if (more && L + 1 >= job->max_levels) set_status(ctl, TSQS_EINTERNAL);
-    const uint32_t cont = (ctl->status == 0u && more) ? 1u : 0u;
+    const uint32_t go = (ctl->status == 0u && more) ? 1u : 0u;
+    const uint32_t cont = (go && ctl->nleaf <= job->leaf_defer) ? 1u : 0u;
+    ctl->more = go;
     ctl->cont = cont;
     if (use_handle) cudaGraphSetConditional(handle, cont);
 }

@@ -144,7 +144,7 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
             return TSQS_ECUDA;
         // the loop flag comes back into ordinary host memory: the copy returns once the
         // level is done
-        if (cudaMemcpyAsync(&g_cont[dev], &d.ctl->cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(&g_cont[dev], &d.ctl->more, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return TSQS_ECUDA;
         if (!g_cont[dev]) break;
