@@ -1015,7 +1015,7 @@ int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_k
     char *misc = c->scratch + L.misc_off;
     uint64_t *d_offs = (uint64_t *)misc;
     uint64_t *d_pos = (uint64_t *)(misc + 64);
-    void *d_piv = misc + 64 + 8 * kMaxSamples + 64;
+    void *d_piv = misc + 1024;                       // 16-byte aligned (records)
     const uint64_t offs[2] = {seg_begin, seg_end};
     if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
     CK(cudaMemcpyAsync(d_offs, offs, sizeof(offs), cudaMemcpyHostToDevice, s));
