@@ -133,3 +133,31 @@ def test_full_batched_20000_segments(T, orc):
         exp = x[b:e].copy()
         orc.tsqs_sort(exp, 1)
         assert got[b:e].tobytes() == exp.tobytes(), f"segment {s}"
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_largest_segment_2e31_minus_1(T, mode):
+    """The largest segment the boundary accepts (2^31 - 1 int32): tile ids, per-tile
+    counts, per-segment cursors and look-back words all run at their widest.  Checked on
+    the device by properties (in order; equal to a library sort of the input)."""
+    import ctypes
+    n = (1 << 31) - 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < 48 * (1 << 30):
+        pytest.skip("needs about 48 GB of device memory")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(31 + mode)
+    src = torch.randint(-2**31, 2**31, (n,), dtype=torch.int64, device="cuda", generator=g).to(torch.int32)
+    plan = T.Plan()
+    T.lib().tsqs_plan_default(T.TSQS_I32, n, ctypes.byref(plan))
+    plan.offset_mode = mode
+    ctx = T.Context(plan)
+    t = src.clone()
+    T.sort_(t, kind=T.TSQS_I32, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert bool((t[1:] >= t[:-1]).all().item())
+    ref = torch.sort(src)[0]
+    del src
+    assert torch.equal(t, ref)
+    ctx.close()
