@@ -511,3 +511,23 @@ def test_presorted_many_segments_checked_concurrently(T, orc):
     exp = a.copy()
     orc.tsqs_sort_segments(exp, offs.astype(np.uint64), 1, threads=4)
     assert from_dev(t, np.int32).tobytes() == exp.tobytes()
+
+
+def test_segmented_half_a_million_segments(T, orc):
+    """Very many segments (most below 64 elements, a few above the on-chip threshold):
+    the init pushes and the leaf queue are sized by the segment count."""
+    rng = np.random.default_rng(77)
+    nseg = 500_000
+    sizes = rng.integers(0, 64, nseg).astype(np.int64)
+    sizes[rng.integers(0, nseg, 40)] = rng.integers(4097, 300_000, 40)
+    offs = np.zeros(nseg + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    x = int32_pattern("random", int(offs[-1]), seed=78)
+    x[::9] = 5
+    t = to_dev(x)
+    T.sort_segmented_(t, torch.from_numpy(offs).cuda(), kind=1)
+    torch.cuda.synchronize()
+    assert T.last_device_status() == 0
+    exp = x.copy()
+    orc.tsqs_sort_segments(exp, offs.astype(np.uint64), 1, threads=4)
+    assert from_dev(t, np.int32).tobytes() == exp.tobytes()
