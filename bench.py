@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="one instrumented (host-driven, one launch per kernel) sort of the "
                          "uniform workload and nothing else: the case the ncu captures use")
+    ap.add_argument("--kind", default="i32", choices=["i32", "i64", "rec"],
+                    help="with --profile: int32, int64 (uniform 64-bit) or {u64, u64} records")
     return ap.parse_args()
 
 
@@ -291,18 +293,33 @@ def profile_case(args, dist):
     import torch
     torch.cuda.set_device(dist.local)
     import paper_1505_00558_gb300 as T
-    from workloads import int32_pattern
+    from workloads import int32_pattern, records_u64
+    from workloads.patterns import rand_u64
     n = args.n
-    src = torch.from_numpy(int32_pattern("random", n, seed=1)).cuda()
+    if args.kind == "rec":
+        kind, label = T.TSQS_U64_U64_REC, "{u64, u64} records"
+        src = torch.from_numpy(records_u64(n, seed=1).view(np.int64).copy()).cuda()
+    elif args.kind == "i64":
+        kind, label = T.TSQS_I64, "int64 uniform random"
+        src = torch.from_numpy(rand_u64(1, 64, n).view(np.int64)).cuda()
+    else:
+        kind, label = T.TSQS_I32, "int32 uniform random"
+        src = torch.from_numpy(int32_pattern("random", n, seed=1)).cuda()
     plan = T.Plan()
-    T.lib().tsqs_plan_default(T.TSQS_I32, n, ctypes.byref(plan))
+    T.lib().tsqs_plan_default(kind, n, ctypes.byref(plan))
     plan.offset_mode = 1 if args.lookback else 0
     ctx = T.Context(plan)
-    ms, keys, lms = ctx.sort_timed(src, kind=T.TSQS_I32)
+    ms, keys, lms = ctx.sort_timed(src, kind=kind)
     torch.cuda.synchronize()
-    ok = ctx.status() == 0 and bool((src[1:] >= src[:-1]).all().item())
+    if kind == T.TSQS_U64_U64_REC:
+        # (key, payload) in order as unsigned 64-bit words: flip the sign bits, compare signed
+        flip = torch.tensor(-(1 << 63), dtype=torch.int64, device=src.device)
+        k, p = src[:, 0] ^ flip, src[:, 1] ^ flip
+        ok = ctx.status() == 0 and bool(((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (p[1:] >= p[:-1]))).all().item())
+    else:
+        ok = ctx.status() == 0 and bool((src[1:] >= src[:-1]).all().item())
     if dist.rank == 0:
-        print(json.dumps({"profile_case": f"{size_label(n)} int32 uniform random seed 1",
+        print(json.dumps({"profile_case": f"{size_label(n)} {label} seed 1",
                           "levels": len(ms), "leaf_launches": len(ms) + 1, "sorted": ok,
                           "partition_ms": [round(m, 4) for m in ms],
                           "leaf_ms": [round(m, 4) for m in lms]}), flush=True)
