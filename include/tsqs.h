@@ -122,7 +122,8 @@ int tsqs_sort_segmented(void *base, size_t nmemb_total, const uint64_t *d_seg_of
  * mapped (cudaHostAlloc / cudaHostRegister / a pinned torch tensor), the kernels write
  * the sorted result straight into h_base, so the last on-chip pass overlaps the
  * transfer back; any other host array is copied back after the sort.  Synchronises
- * `stream` before returning. */
+ * `stream` before returning.  For a sequence of host arrays, tsqs_ctx_sort_host_stream
+ * overlaps the copies of neighbouring arrays with the sorts. */
 int tsqs_sort_host(void *h_base, size_t nmemb, size_t elem_size, int key_kind, void *stream);
 
 /* Large elements (Section VIII.G-H, "late swapping"; the qsort of an array of wide
