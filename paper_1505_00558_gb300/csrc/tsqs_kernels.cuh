@@ -1097,7 +1097,14 @@ __device__ __forceinline__ void cx(C &lo, C &hi) {
     hi = c_maxv(a, b);
 }
 
-__device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
+// Padded shared-memory index of element i of a sort buffer of C: one pad element after
+// every 128 bytes of elements (32 four-byte, 16 eight-byte or 8 sixteen-byte ones).  Shared
+// memory serves a warp's 4-, 8- and 16-byte accesses in phases of 32, 16 and 8 lanes; lane
+// t of a network stage touches element E t + r, so with one pad per 128 bytes the lanes of a
+// phase fall in distinct bank groups.
+template <class C> constexpr uint32_t kPadGroup = 128u / (uint32_t)sizeof(C);
+template <class C>
+__device__ __forceinline__ uint32_t padc(uint32_t i) { return i + i / kPadGroup<C>; }
 
 // Sorts s[0, P) ascending; P a power of two with 32 E <= P <= E * blockDim.x, and
 // s[len, P) holding the largest key.  Every thread of the block must call it (it
@@ -1113,7 +1120,7 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
     C v[E];
     if (act) {
 #pragma unroll
-        for (int r = 0; r < E; r++) v[r] = s[pad32(t * E + r)];
+        for (int r = 0; r < E; r++) v[r] = s[padc<C>(t * E + r)];
         // merges of width k <= E: inside the thread
 #pragma unroll
         for (int k = 2; k <= E; k <<= 1) {
@@ -1150,14 +1157,14 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
             __syncthreads();
             if (act) {
 #pragma unroll
-                for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+                for (int r = 0; r < E; r++) s[padc<C>(t * E + r)] = v[r];
             }
             __syncthreads();
             if (act) {
                 const bool lower = ((t * E) & (k >> 1)) == 0u;
 #pragma unroll
                 for (int r = 0; r < E; r++) {
-                    const C w = s[pad32((t * E + r) ^ (k - 1))];
+                    const C w = s[padc<C>((t * E + r) ^ (k - 1))];
                     v[r] = cx_side(v[r], w, lower);
                 }
             }
@@ -1167,14 +1174,14 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
             __syncthreads();
             if (act) {
 #pragma unroll
-                for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+                for (int r = 0; r < E; r++) s[padc<C>(t * E + r)] = v[r];
             }
             __syncthreads();
             if (act) {
                 const bool lower = ((t * E) & j) == 0u;
 #pragma unroll
                 for (int r = 0; r < E; r++) {
-                    const C w = s[pad32((t * E + r) ^ j)];
+                    const C w = s[padc<C>((t * E + r) ^ j)];
                     v[r] = cx_side(v[r], w, lower);
                 }
             }
@@ -1235,7 +1242,7 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
     __syncthreads();
     if (act) {
 #pragma unroll
-        for (int r = 0; r < E; r++) s[pad32(t * E + r)] = v[r];
+        for (int r = 0; r < E; r++) s[padc<C>(t * E + r)] = v[r];
     }
     __syncthreads();
 }
@@ -1247,7 +1254,7 @@ struct LeafLayout {
     using S = typename Key<KIND>::S;
     using C = typename Key<KIND>::C;
     static constexpr int PRE = kMaxSmall + 2 * Key<KIND>::V;          // elements per slot
-    static constexpr size_t sort_bytes = ((kMaxSmall + kMaxSmall / 32) * sizeof(C) + 127) / 128 * 128;
+    static constexpr size_t sort_bytes = ((kMaxSmall + kMaxSmall / kPadGroup<C>) * sizeof(C) + 127) / 128 * 128;
     static constexpr size_t off_pre = sort_bytes;
     // one prefetch slot: an item's keys leave it for the sort buffer before the next
     // item's bulk copy is issued into it, so a second slot would only cost occupancy
@@ -1342,7 +1349,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
                     const int64_t e = (int64_t)it.begin + i;
                     c = K::canon((e >= cs && e < ce) ? slot[e - cs] : src[e]);
                 }
-                s[pad32(i)] = c;
+                s[padc<C>(i)] = c;
             }
         }
         fence_proxy_async();                // this slot's reads precede its next bulk copy
@@ -1372,7 +1379,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P, it.len);
             else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P, it.len);
             else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P, it.len);
-            for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = K::uncanon(s[pad32(i)]);
+            for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = K::uncanon(s[padc<C>(i)]);
             sorted += it.len;
         }
         __syncthreads();                    // sort buffer free, next item's meta visible
@@ -1528,7 +1535,7 @@ __device__ __forceinline__ void deep_tile_network(C *sm, bool full) {
         if (full && k <= (uint32_t)kDeepTile) {
             for (uint32_t q = t; q < (uint32_t)kDeepTile / 2; q += blockDim.x) {    // mirror
                 const uint32_t half = k >> 1, i = (q / half) * k + (q % half), p = i ^ (k - 1u);
-                cx(sm[pad32(i)], sm[pad32(p)]);
+                cx(sm[padc<C>(i)], sm[padc<C>(p)]);
             }
             __syncthreads();
         }
@@ -1536,7 +1543,7 @@ __device__ __forceinline__ void deep_tile_network(C *sm, bool full) {
         for (uint32_t j = jtop; j >= 1u; j >>= 1) {
             for (uint32_t q = t; q < (uint32_t)kDeepTile / 2; q += blockDim.x) {
                 const uint32_t i = (q / j) * 2u * j + (q % j);
-                cx(sm[pad32(i)], sm[pad32(i + j)]);
+                cx(sm[padc<C>(i)], sm[padc<C>(i + j)]);
             }
             __syncthreads();
         }
@@ -1554,10 +1561,10 @@ __device__ __forceinline__ void deep_tile(const Job *job, const LeafItem &it, ui
     const uint64_t base = (uint64_t)ti * kDeepTile;
     const uint32_t cnt = (uint32_t)min((uint64_t)kDeepTile, (uint64_t)it.len - base);
     for (uint32_t i = threadIdx.x; i < (uint32_t)kDeepTile; i += blockDim.x)
-        sm[pad32(i)] = i < cnt ? K::canon(buf[base + i]) : c_max<typename K::C>();
+        sm[padc<typename K::C>(i)] = i < cnt ? K::canon(buf[base + i]) : c_max<typename K::C>();
     __syncthreads();
     deep_tile_network(sm, full);
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) buf[base + i] = K::uncanon(sm[pad32(i)]);
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) buf[base + i] = K::uncanon(sm[padc<typename K::C>(i)]);
     __syncthreads();
 }
 
