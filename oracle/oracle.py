@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
             L.orc_classical_sort.argtypes = [vp, sz, i, u64, ps]
             L.orc_juggle_sort.argtypes = [vp, sz, i, u64, ps]
             L.orc_median3.argtypes = [vp, sz, sz, sz, i, ps]
+            L.orc_choose_pivot.argtypes = [vp, sz, i, pc, ps]
+            L.orc_choose_pivot.restype = ctypes.c_longlong
             L.orc_lower_median.argtypes = [vp, sz, i, vp]
             L.orc_three_way_split.argtypes = [vp, vp, sz, i, vp, ctypes.POINTER(sz),
                                               ctypes.POINTER(sz), ctypes.POINTER(sz)]
@@ -171,6 +173,18 @@ def median3(a: np.ndarray, kind: int, i0: int = 0, i1: int = 1, i2: int = 2) -> 
     st = _Stats()
     o = lib().orc_median3(a.ctypes.data, i0, i1, i2, kind, ctypes.byref(st))
     return o, st.as_dict()
+
+
+def choose_pivot(a: np.ndarray, kind: int, cfg: OracleCfg | None = None) -> tuple[int, dict]:
+    """Pivot selection of Section III.H alone on the part ``a`` (in place: the tier's
+    samples end sorted); returns the pivot index and the counters."""
+    n = _check(a, kind)
+    st = _Stats()
+    c = (cfg or OracleCfg())._c()
+    pi = lib().orc_choose_pivot(a.ctypes.data, n, kind, ctypes.byref(c), ctypes.byref(st))
+    if pi < 0:
+        raise ValueError("choose_pivot needs n >= 3 and a known key kind")
+    return int(pi), st.as_dict()
 
 
 def lower_median(keys: np.ndarray, kind: int) -> np.ndarray:

@@ -1002,6 +1002,22 @@ int orc_tsqs_stage(void *base, size_t n, int key_kind, size_t pi, orc_stats *st,
     return 0;
 }
 
+/* Pivot selection alone on base[0..n): the tier choice of Section III.H for a part
+ * [0, n-1] with mid = (n-1)/2, under cfg (NULL = defaults).  The samples are sorted in
+ * place as in a stage; returns the pivot index, or -1 on bad arguments. */
+long long orc_choose_pivot(void *base, size_t n, int key_kind, const orc_cfg *cfg,
+                           orc_stats *st) {
+    orc_stats local;
+    if (!st) { memset(&local, 0, sizeof(local)); st = &local; }
+    if (n < 3) return -1;
+    tctx c;
+    if (ctx_init(&c, base, n, key_kind, cfg, st)) return -1;
+    idx b = (idx)n - 1, mid = b / 2;
+    idx pi = choose_pivot(&c, 0, b, mid);
+    ctx_free(&c);
+    return (long long)pi;
+}
+
 /* One textbook Hoare stage with the pivot at index pi; counts cmps and exchanges. */
 int orc_hoare_stage(void *base, size_t n, int key_kind, size_t pi, orc_stats *st) {
     orc_stats local;

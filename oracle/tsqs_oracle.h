@@ -133,6 +133,12 @@ int orc_juggle_sort(void *base, size_t n, int key_kind, uint64_t seed, orc_stats
 int orc_tsqs_stage(void *base, size_t n, int key_kind, size_t pi, orc_stats *st,
                    long long *lo, long long *hi);
 
+/* Pivot selection alone (Section III.H tiers) on the part base[0..n), n >= 3, with
+ * mid = (n-1)/2: sorts the tier's samples in place exactly as a stage would and
+ * returns the pivot index (-1 on bad arguments).  Counts its cmps and moves in st. */
+long long orc_choose_pivot(void *base, size_t n, int key_kind, const orc_cfg *cfg,
+                           orc_stats *st);
+
 /* One textbook Hoare stage (as in orc_classical_sort) with the pivot at index pi. */
 int orc_hoare_stage(void *base, size_t n, int key_kind, size_t pi, orc_stats *st);
 

@@ -36,15 +36,24 @@ MUTATIONS = {
     "wide_tie_unstable": ("return px < py ? -1 : (px > py ? 1 : 0);", "return 0;"),
     # late swapping: a cycle member not marked placed is walked again
     "wide_cycle_unmarked": ("            placed[src] = 1;\n", ""),
+    # counters: the insertion sort (Section IV) counts its copy into temp twice
+    "insertion_double_count": ("ccopy(c, c->temp, AR(c, j));",
+                               "ccopy(c, c->temp, AR(c, j)); c->st->moves++;"),
+    # counters: the median-of-five insertion over the sample positions counts a copy twice
+    "pivot_double_count": ("ccopy(c, c->scratch, AR(c, pos[s]));",
+                           "ccopy(c, c->scratch, AR(c, pos[s])); c->st->moves++;"),
+    # counters: State 1 counts the copy of a larger element into the hole at r twice
+    "stage_double_count": ("ccopy(c, AR(c, r), AR(c, l));\n                r--;\n                state = (mr == r)",
+                           "ccopy(c, AR(c, r), AR(c, l)); c->st->moves++;\n                r--;\n                state = (mr == r)"),
 }
 
 
 def _build_mutant(name, tmpdir):
-    old, new = MUTATIONS[name]
+    old, new = MUTATIONS[name] if name else ("", "")
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    assert not name or src.count(old) == 1, f"mutation site for {name} not unique"
     path = os.path.join(tmpdir, f"m_{name}.c")
-    open(path, "w").write(src.replace(old, new))
+    open(path, "w").write(src.replace(old, new) if name else src)
     hdr_dir = os.path.dirname(SRC)
     so = os.path.join(tmpdir, f"m_{name}.so")
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-I", hdr_dir,
@@ -107,12 +116,24 @@ def _exhaustive_fails(L) -> bool:
     return False
 
 
+def _counts_fail(L) -> bool:
+    """The counter pins of tests/test_oracle_counts.py, the whole-sort ones at reduced
+    size (40 permutations at n = 10^4 and 10^5)."""
+    from tests.test_oracle_counts import (bind, insertion_sort_counts_fail, pivot_counts_fail,
+                                          whole_sort_fail, whole_sort_means)
+    bind(L)
+    if insertion_sort_counts_fail(L) or pivot_counts_fail(L):
+        return True
+    means = {n: whole_sort_means(L, n, 40, full=False) for n in (10 ** 4, 10 ** 5)}
+    return whole_sort_fail(means) is not None
+
+
 def _run_child(name: str) -> int:
     """Child process: exit 0 if the mutant passes every check (escaped), 1 if a check
     failed.  A mutant that crashes or loops ends the child some other way."""
     with tempfile.TemporaryDirectory() as d:
         L = _build_mutant(name, d)
-        return 1 if _exhaustive_fails(L) else 0
+        return 1 if (_exhaustive_fails(L) or _counts_fail(L)) else 0
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -126,3 +147,13 @@ def test_planted_mistake_is_caught(name):
     except subprocess.TimeoutExpired:
         rc = -1                                   # the mutant looped: caught
     assert rc != 0, f"mutation {name} escaped the pins"
+
+
+def test_unmutated_oracle_passes_every_check():
+    """Control: the same checks on an unmutated copy all pass, so a caught mutant is
+    caught by its mistake and not by a check that fails anyway."""
+    root = os.path.dirname(os.path.dirname(SRC))
+    code = ("import sys; sys.path.insert(0, %r); from tests.test_oracle_mutations import _run_child; "
+            "sys.exit(_run_child(''))" % root)
+    rc = subprocess.run([sys.executable, "-c", code], timeout=300, capture_output=True).returncode
+    assert rc == 0
