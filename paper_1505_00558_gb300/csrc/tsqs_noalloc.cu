@@ -1,15 +1,20 @@
 // tsqs_noalloc.cu -- a sort entry point that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at the moment they need a sort: code running
-// while a CUDA stream capture is active (allocation there is refused or breaks the
-// capture), code whose device memory is entirely owned by another allocator (a
-// framework's caching pool, a fixed arena), and latency-critical paths that cannot
-// pay for an allocation that may synchronise the device.  tsqs_sort_noalloc serves
-// them: it runs the same kernels as tsqs_sort, but every piece of scratch -- the
-// second buffer of the ping-pong, the segment and leaf queues, the tile table, the
-// per-call description and the control block -- lives in the static device arrays
-// below, which are part of this library's device code.  Each GPU on which this code
-// is loaded holds the arrays until the process exits.
+// Some callers cannot call cudaMalloc at the moment they need a sort: code whose
+// device memory is entirely owned by another allocator (a framework's caching pool,
+// a fixed arena, where a raw cudaMalloc fails or fragments it), services that account
+// for every device byte up front, and latency-critical paths that cannot pay for an
+// allocation that may synchronise the device.  tsqs_sort_noalloc serves them: it runs
+// the same kernels as tsqs_sort, but every piece of scratch -- the second buffer of
+// the ping-pong, the segment and leaf queues, the tile table, the per-call description
+// and the control block -- lives in the static device arrays below, which are part of
+// this library's device code.  Each GPU on which this code is loaded holds the arrays
+// until the process exits.
+//
+// The call drives the level loop from the host: it reads the loop flag back and
+// synchronises `stream` after every level, and it returns only once its sort has
+// finished.  A stream that is being captured cannot be synchronised, so the call
+// refuses one (TSQS_EINVAL, nothing queued).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -101,11 +106,14 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
     if (!o || (size_t)o->elem_size != elem_size) return TSQS_EINVAL;
     if (nmemb > 1 && !base) return TSQS_EINVAL;
     if ((uintptr_t)base % (elem_size == 16 ? 16 : elem_size)) return TSQS_EINVAL;
-    if (nmemb * elem_size > TSQS_NOALLOC_MAX_BYTES) return TSQS_EINVAL;   // over the limit
+    if (nmemb > TSQS_NOALLOC_MAX_BYTES / elem_size) return TSQS_EINVAL;   // over the limit
     if (nmemb <= 1) return TSQS_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TSQS_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) { cudaGetLastError(); return TSQS_EINVAL; }
+    if (cap != cudaStreamCaptureStatusNone) return TSQS_EINVAL;          // would break the capture
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &d = g_dev[dev];
     int rc = setup_device(dev, d);
@@ -125,15 +133,21 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
     int leaf_final = 0, leaf_last = 1;
     void *argsl[] = {&pj, &pc, &leaf_final};
     void *argsl_last[] = {&pj, &pc, &leaf_last};
+    int use_hd = 0;
+    void *argsd[] = {&pj, &pc, &h, &use_hd};
+    uint32_t status = 0;
     // setup zeroes the control block, so nothing a previous call left in the shared
     // arrays is read before it is rewritten
     k_setup<<<1, 256, 0, s>>>(d.job, d.ctl, j);
-    if (cudaGetLastError() != cudaSuccess) return TSQS_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) goto failed;
+    // from here on every failure goes through `failed`, which waits for the kernels
+    // already queued before the lock is released, so a later call never rewrites the
+    // shared arrays under them
     if (cudaLaunchKernel(o->k_orient, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
         cudaLaunchKernel(o->k_check, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
         cudaLaunchKernel(o->k_presort, dim3(d.sms * 4), dim3(256), args2, 0, s) != cudaSuccess ||
         cudaLaunchKernel(o->k_init, dim3(d.sms * 2), dim3(256), args2, 0, s) != cudaSuccess)
-        return TSQS_ECUDA;
+        goto failed;
     for (uint32_t level = 0; level <= j.max_levels; level++) {
         if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl,
                              (size_t)o->leaf_smem, s) != cudaSuccess ||
@@ -141,37 +155,39 @@ extern "C" int tsqs_sort_noalloc(void *base, size_t nmemb, size_t elem_size, int
             cudaLaunchKernel(pv.k_partition, dim3(d.part_grid[key_kind]), dim3(pv.threads), args2,
                              (size_t)pv.smem, s) != cudaSuccess ||
             cudaLaunchKernel(o->k_finish, dim3(d.sms), dim3(128), argsf, 0, s) != cudaSuccess)
-            return TSQS_ECUDA;
+            goto failed;
         // the loop flag comes back into ordinary host memory: the copy returns once the
         // level is done
         if (cudaMemcpyAsync(&g_cont[dev], &d.ctl->more, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
-            return TSQS_ECUDA;
+            goto failed;
         if (!g_cont[dev]) break;
     }
     // the final leaf pass over every queued item
     if (cudaLaunchKernel(o->k_leaf, dim3(d.leaf_grid[key_kind]), dim3(o->leaf_block), argsl_last,
                          (size_t)o->leaf_smem, s) != cudaSuccess)
-        return TSQS_ECUDA;
+        goto failed;
     // depth guard: segments that reached the level bound are sorted by the bitonic stages
-    int use_hd = 0;
-    void *argsd[] = {&pj, &pc, &h, &use_hd};
     if (cudaLaunchKernel(o->k_deep_prep, dim3(1), dim3(512), argsd, 0, s) != cudaSuccess ||
         cudaLaunchKernel(o->k_deep_tiles, dim3(d.sms * 2), dim3(512), args2, (size_t)o->deep_smem, s) != cudaSuccess)
-        return TSQS_ECUDA;
+        goto failed;
     for (int it = 0; it < 4096; it++) {
         if (cudaMemcpyAsync(&g_cont[dev], &d.ctl->deep_cont, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
-            return TSQS_ECUDA;
+            goto failed;
         if (!g_cont[dev]) break;
         if (cudaLaunchKernel(o->k_deep_stage, dim3(d.sms * 2), dim3(512), argsd, (size_t)o->deep_smem, s) != cudaSuccess)
-            return TSQS_ECUDA;
+            goto failed;
     }
     if (cudaLaunchKernel(o->k_deep_finish, dim3(d.sms * 2), dim3(512), args2, 0, s) != cudaSuccess)
-        return TSQS_ECUDA;
-    uint32_t status = 0;
+        goto failed;
     if (cudaMemcpyAsync(&status, &d.ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return TSQS_ECUDA;
+        goto failed;
     return (int)status;
+failed:
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return TSQS_ECUDA;
 }

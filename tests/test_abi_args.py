@@ -61,6 +61,10 @@ def test_context_and_noalloc_arguments(T, host_buf):
     assert L.tsqs_sort_noalloc(vp(p), over, 4, T.TSQS_I32, None) == T.TSQS_EINVAL
     assert L.tsqs_sort_noalloc(vp(p), 100, 8, T.TSQS_I32, None) == T.TSQS_EINVAL
     assert L.tsqs_sort_noalloc(vp(p), 1, 4, T.TSQS_I32, None) == T.TSQS_OK
+    # sizes whose byte count wraps around 2^64 are over the limit too
+    huge = (1 << 64) // 4 + 1
+    assert L.tsqs_sort_noalloc(vp(p), huge, 4, T.TSQS_I32, None) == T.TSQS_EINVAL
+    assert L.tsqs_sort_noalloc(vp(p), (1 << 64) // 16 + 3, 16, T.TSQS_U64_U64_REC, None) == T.TSQS_EINVAL
 
 
 def test_wide_and_host_stream_arguments(T, host_buf):
