@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_HEADLINE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the compact timing of the other configurations in the headline line")
     ap.add_argument("--lookback", action="store_true",
                     help="with --profile: decoupled look-back offsets, whose layout (and so the "
                          "level count) does not depend on timing")
@@ -201,24 +203,70 @@ class ClockSampler:
 # CPU legs (oracle; the only places bench.py runs oracle/)
 # ------------------------------------------------------------------------------
 
-def oracle_rate(keys: np.ndarray, budget_s: float = 12.0, chunk: int = 1 << 24):
-    """Times the oracle single-threaded on consecutive chunks of keys (each chunk is
-    sorted on its own) until budget_s of CPU time; returns (Mkeys/s, sample text)."""
+def host_info() -> dict:
+    """Host core count and CPU model of the box the bench runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or None,
+            "machine": platform.machine()}
+
+
+class PinnedCore:
+    """Runs the calling thread on one host core (the first it is allowed), so that the
+    CPU references are single-threaded on the same core; restores the mask after."""
+
+    def __enter__(self):
+        self.mask = os.sched_getaffinity(0)
+        self.core = min(self.mask)
+        os.sched_setaffinity(0, {self.core})
+        return self
+
+    def __exit__(self, *exc):
+        os.sched_setaffinity(0, self.mask)
+
+
+def cpu_baselines(keys: np.ndarray) -> dict:
+    """The oracle single-threaded on the whole workload once, and std::sort on the same
+    core as a second (library) reference; Mkeys/s and seconds of each."""
     import oracle
     oracle.build()
-    done, t_tot, chunks = 0, 0.0, 0
-    off = 0
-    while t_tot < budget_s and off < len(keys):
-        part = np.ascontiguousarray(keys[off:off + chunk].copy())
+    info = host_info()
+    with PinnedCore() as pc:
+        a = keys.copy()
         t0 = time.perf_counter()
-        oracle.tsqs_sort(part, oracle.KIND_I32)
-        t_tot += time.perf_counter() - t0
-        done += len(part)
-        off += chunk
-        chunks += 1
-    sample = (f"{chunks} independent sorts of {chunk} keys (the first {done} keys of the "
-              f"workload), oracle single-threaded")
-    return done / t_tot / 1e6, sample, t_tot
+        oracle.tsqs_sort(a, oracle.KIND_I32)
+        t_orc = time.perf_counter() - t0
+        b = keys.copy()
+        t0 = time.perf_counter()
+        oracle.std_sort_i32(b)
+        t_std = time.perf_counter() - t0
+    same = bool(np.array_equal(a, b))
+    n = len(keys)
+    return {"value": n / t_orc / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the whole workload ({n} keys) sorted once by the oracle, single-threaded "
+                      f"on host core {pc.core}",
+            "seconds": t_orc,
+            "std_sort": {"value": n / t_std / 1e6, "unit": UNIT, "seconds": t_std, "cores": 1,
+                         "kind": "std::sort (g++ -O2), same core, same input",
+                         "same_result_as_oracle": same},
+            "host": info}
 
 
 def reference_arm(args, dist):
@@ -250,7 +298,7 @@ def reference_arm(args, dist):
             "config": {"workload": "2^27 int32 uniform random seed 1 (bounded sample per step)",
                        "n_per_step": chunk},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -451,11 +499,13 @@ def gpu_arm(args, dist):
                                "value": dist.sum(float(len(times) * n)) / ts / 1e6,
                                "ms": ts * 1e3 / len(times), "sorted": single_ok}}
 
+    configs = None
+    if not args.no_configs:
+        configs = other_configs(torch, T, hbm)
+
     cpu = None
     if dist.rank == 0 and not args.no_cpu_baseline:
-        rate, sample, t_cpu = oracle_rate(x, budget_s=10.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": t_cpu}
+        cpu = cpu_baselines(x)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": K, "warmup": W, "ms_per_step": ms_step, "higher_is_better": True,
@@ -465,6 +515,7 @@ def gpu_arm(args, dist):
                        "l2": "inputs larger than L2: every step sorts its own fresh 512 MiB copy",
                        "small_threshold": SMALL_T},
             "roofline": roofline, "roofline_whole_sort": whole, "cpu_baseline": cpu,
+            "configs": configs,
             "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_sort * K,
             "sorted": ok, "device_status": status,
             "per_step_ms": {"median": statistics.median(per), "min": min(per), "max": max(per)},
@@ -473,10 +524,58 @@ def gpu_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
-def _time_fresh(torch, T, src, kind, reps, records=False, ctx=None):
+def other_configs(torch, T, hbm: float) -> dict:
+    """Compact timings of the other configurations for the headline line: 1e6 int32
+    (latency), the six other 2^27 int32 orderings, 2^26 records and 2^26 float32 under
+    totalOrder.  Each: one warm-up sort, then the median of a few timed sorts of fresh
+    copies (CUDA events; every input but the 1e6 one is larger than L2)."""
+    from workloads import PATTERNS, int32_pattern, records_u64, floats_normal_specials
+    out = {}
+
+    def one(name, src, kind, n, es, reps, desc):
+        med, best, ok, w = _time_fresh(torch, T, src, kind, reps, warm=1)
+        if es == 16:
+            flip = torch.tensor(-(1 << 63), dtype=torch.int64, device=w.device)
+            k, p = w[:, 0] ^ flip, w[:, 1] ^ flip
+            ok = ok and bool(((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (p[1:] >= p[:-1]))).all().item())
+        elif kind == T.TSQS_F32:
+            u = w.view(torch.int32)
+            key = torch.where(u < 0, u ^ 0x7FFFFFFF, u)        # totalOrder as signed ints
+            ok = ok and bool((key[1:] >= key[:-1]).all().item())
+        else:
+            ok = ok and bool((w[1:] >= w[:-1]).all().item())
+        pm = p_min(n)
+        out[name] = {"workload": desc, "ms": med, "best_ms": best, "mkeys_s": n / med / 1e3,
+                     "sorted": ok,
+                     "frac_whole_sort_of_measured": pm * 2 * n * es / (med * 1e-3) / 1e9 / hbm}
+        del w
+
+    src = torch.from_numpy(int32_pattern("random", 1_000_000, seed=1)).cuda()
+    one("c1_1e6_int32", src, T.TSQS_I32, 1_000_000, 4, 10,
+        "1e6 int32 uniform random seed 1 (L2-resident: latency, not a roofline case)")
+    n = N_HEADLINE
+    for p in PATTERNS:
+        if p == "random":
+            continue
+        src = torch.from_numpy(int32_pattern(p, n, seed=1)).cuda()
+        one(f"c2_{p}", src, T.TSQS_I32, n, 4, 2, f"2^27 int32 {p}, seed 1")
+        del src
+    src = torch.from_numpy(records_u64(1 << 26, seed=1).view(np.int64)).cuda()
+    one("c3a_records", src, T.TSQS_U64_U64_REC, 1 << 26, 16, 2,
+        "2^26 {u64 key, u64 payload}, 10% duplicated keys, 0.1% duplicated records")
+    del src
+    src = torch.from_numpy(floats_normal_specials(1 << 26, seed=1)).cuda()
+    one("c3b_float32", src, T.TSQS_F32, 1 << 26, 4, 2,
+        "2^26 float32 ~N(0,1) with 0.1% +-0, +-inf, NaNs (IEEE totalOrder)")
+    del src
+    torch.cuda.empty_cache()
+    return out
+
+
+def _time_fresh(torch, T, src, kind, reps, records=False, ctx=None, warm=2):
     """Median / best ms of sorting fresh copies of src (copy outside the events)."""
     ts = []
-    for r in range(reps + 2):
+    for r in range(reps + warm):
         w = src.clone()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -485,7 +584,7 @@ def _time_fresh(torch, T, src, kind, reps, records=False, ctx=None):
         T.sort_(w, kind=kind, ctx=ctx)
         e1.record()
         torch.cuda.synchronize()
-        if r >= 2:
+        if r >= warm:
             ts.append(e0.elapsed_time(e1))
     status = T.last_device_status() if ctx is None else ctx.status()
     ok = status == 0
@@ -683,15 +782,19 @@ def _gen_request(torch, kind_rec, n, pattern, seed, dev):
 def serving_workload(args, dist, torch, T):
     """Poisson stream of 50,000 sort requests, sizes floor(2^(10 + 14U)), 70% int32 /
     30% (u64, u64) records, patterns from the seven, admitted under a 40 GB budget.
-    The offered load is 0.7 x the sustained throughput measured with the requests
-    submitted as fast as buffers free up.  Request contents come from a pool of 2,000
-    distinct generated requests: request i sorts a fresh copy of pool entry i mod 2000
-    (its buffer is restored once request i - 2000 on it has finished); the arrival
-    gaps are drawn for all 50,000."""
+    The offered load is 0.7 x the sustained throughput measured with every request
+    arriving at once.  Request contents come from a pool of 2,000 distinct generated
+    requests: request i sorts pool entry i mod 2000 in a work buffer of its own, which is
+    refilled from the pristine copy as soon as request i - 2000 on it has finished (off
+    the submission path; a request whose buffer is not refilled yet when it arrives
+    counts as a pool stall).  Latency is measured from the request's Poisson arrival
+    time to its completion, on the host's monotonic clock; the time from submission to
+    completion is reported beside it."""
     from workloads import PATTERNS
     from workloads.patterns import serving_requests
     nreq = int(os.environ.get("TSQS_SERVE_REQUESTS", "50000"))
     npool = min(nreq, int(os.environ.get("TSQS_SERVE_POOL", "2000")))
+    budget, lanes = 40 << 30, 4
     req = serving_requests(nreq, seed=1)
     dev = torch.device("cuda")
     pristine = []
@@ -701,37 +804,51 @@ def serving_workload(args, dist, torch, T):
     torch.cuda.synchronize()
     sizes = [int(req["sizes"][i % npool]) for i in range(nreq)]
     is_rec = [bool(req["is_rec"][i % npool]) for i in range(nreq)]
+    nbytes = np.array([s_ * (16 if r_ else 4) for s_, r_ in zip(sizes, is_rec)], dtype=np.float64)
     total_keys = sum(sizes)
     lib = T.lib()
     stream = torch.cuda.current_stream()
 
     def run(lam):
         work = [p.clone() for p in pristine]
+        ready = [None] * npool         # event of the buffer's last refill, until consumed
         torch.cuda.synchronize()
-        srv = lib.tsqs_server_create(40 << 30, 4, 256)
+        srv = lib.tsqs_server_create(budget, lanes, 256)
         assert srv
         arrive = np.cumsum(req["gaps"] / lam) if lam else np.zeros(nreq)
         tickets = [None] * nreq
+        py_sub = np.zeros(nreq)
         r = T.Result()
-        held = 0                       # polls that found an arrival's pool buffer still busy
+        stalls = 0                     # arrivals whose buffer was not refilled yet
+        oldest = 0                     # first request whose buffer has not been refilled
         t0 = time.perf_counter()
         i = 0
         while True:
+            # refill the buffers of finished requests (in submission order), long before
+            # their next request arrives; the copies run on the device, the host goes on
+            while oldest < i and oldest + npool < nreq:
+                lib.tsqs_server_poll(srv, tickets[oldest], ctypes.byref(r))
+                if not r.done:
+                    break
+                j = oldest % npool
+                work[j].copy_(pristine[j])
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                ready[j] = ev
+                oldest += 1
             now = time.perf_counter() - t0
             while i < nreq and arrive[i] <= now:
                 j = i % npool
                 if i >= npool:
-                    # the buffer's previous request must be finished before its reuse
-                    lib.tsqs_server_poll(srv, tickets[i - npool], ctypes.byref(r))
-                    if not r.done:
-                        held += 1
+                    if ready[j] is None or not ready[j].query():
+                        stalls += 1
                         break
-                    work[j].copy_(pristine[j])
-                    stream.synchronize()
+                    ready[j] = None
                 tk = ctypes.c_uint64()
                 kind, es = (T.TSQS_U64_U64_REC, 16) if is_rec[i] else (T.TSQS_I32, 4)
                 rc = lib.tsqs_server_submit(srv, ctypes.c_void_p(work[j].data_ptr()), sizes[i], es,
                                             kind, ctypes.byref(tk))
+                py_sub[i] = time.perf_counter()
                 assert rc == 0, rc
                 tickets[i] = tk.value
                 i += 1
@@ -745,17 +862,38 @@ def serving_workload(args, dist, torch, T):
             res.append((rr.t_submit, rr.t_start, rr.t_done, rr.status, rr.batch_size, rr.batch_id))
         lib.tsqs_server_destroy(srv)
         t_sub = np.array([x[0] for x in res])
+        t_start = np.array([x[1] for x in res])
         t_done = np.array([x[2] for x in res])
-        lat = (t_done - t_sub) * 1e3
-        span = t_done.max() - t_sub.min()
+        # the server stamps times on its own monotonic clock: map the arrivals onto it
+        # by the offset between the two clocks seen at every submission
+        offset = float(np.median(py_sub - t_sub))
+        t_arr = t0 + arrive - offset
+        lat = (t_done - t_arr) * 1e3
+        svc = (t_done - t_sub) * 1e3
+        wait = (t_start - t_arr) * 1e3
+        span = t_done.max() - min(t_arr.min(), t_sub.min())
+        # device bytes of the requests launched and not yet complete, over time
+        ev_t = np.concatenate([t_start, t_done])
+        ev_b = np.concatenate([nbytes, -nbytes])
+        order = np.lexsort((ev_b, ev_t))           # completions before launches at a tie
+        in_flight = np.cumsum(ev_b[order])
         ok = all(x[3] == 0 for x in res)
         sorted_ok = all(bool((w[1:] >= w[:-1]).all().item()) if w.dim() == 1 else True for w in work[:50])
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "sustained_mkeys_s": total_keys / span / 1e6,
+                "mean_ms": float(lat.mean()),
+                "latency": "from the Poisson arrival time to completion",
+                "service_p50_ms": float(np.percentile(svc, 50)),
+                "service_p99_ms": float(np.percentile(svc, 99)),
+                "queue_wait_p99_ms": float(np.percentile(wait, 99)),
+                "sustained_mkeys_s": total_keys / span / 1e6,
                 "span_s": span, "status_ok": ok, "spot_sorted": sorted_ok,
                 "batches": len(set(x[5] for x in res)),
                 "mean_batch": float(np.mean([x[4] for x in res])),
-                "pool_busy_polls": held}
+                "pool_stalls": stalls,
+                "bytes_in_flight_peak": float(in_flight.max()),
+                "bytes_in_flight_mean": float(np.average(
+                    in_flight[:-1], weights=np.diff(ev_t[order]))) if len(in_flight) > 1 else 0.0,
+                "budget_bytes": budget, "lanes": lanes}
 
     run(None)                                             # warm graphs and lanes
     sat = run(None)

@@ -165,6 +165,9 @@ int tsqs_last_device_status(void *stream);
  *   - The first call on a device does the set-up: it looks up the array's device
  *     address with cudaGetSymbolAddress and sets kernel attributes.  Make that first
  *     call before any stream capture begins.
+ *   - The call runs the level loop from the host: it synchronises `stream` after every
+ *     partition level and returns only after the sort has finished.  If `stream` is
+ *     being captured it returns TSQS_EINVAL and queues nothing.
  *   - Every call shares the one array, which keeps the previous call's contents (each
  *     call clears what must start at zero).  Calls whose GPU work overlapped would race
  *     on it; this entry point prevents that within a process by holding a lock for the
@@ -184,6 +187,35 @@ int tsqs_ctx_sort(tsqs_ctx *ctx, void *base, size_t nmemb, size_t elem_size, int
 int tsqs_ctx_sort_segmented(tsqs_ctx *ctx, void *base, size_t nmemb_total,
                             const uint64_t *d_seg_offsets, size_t nseg, size_t elem_size,
                             int key_kind, void *stream);
+/* Caller-held graph of a whole sort (batching, pattern 2: capture once, replay; the
+ * paper's qsort-replacement call of the abstract and Section VII, issued as one CUDA
+ * graph).  graph_exec points to a cudaGraphExec_t passed as void*:
+ *   *graph_exec == NULL  the call builds the whole segmented sort of these arguments as
+ *                        one graph (the per-call setup kernel, then the presortedness
+ *                        kernels, the conditional level loop, the leaf pass and the depth
+ *                        guard), instantiates it into *graph_exec and launches it on
+ *                        `stream`;
+ *   otherwise            *graph_exec must come from an earlier call with the same ctx and
+ *                        key_kind (else TSQS_EINVAL): its setup node is updated to these
+ *                        arguments and it is launched.
+ * d_seg_offsets == NULL sorts base[0, nmemb_total) as one segment; otherwise as
+ * tsqs_ctx_sort_segmented.  Nothing to sort (no segment, or one segment of <= 1
+ * element) returns TSQS_OK with no graph made.  The caller may also replay the graph
+ * itself with cudaGraphLaunch(*graph_exec, s) to sort the same arrays again (after
+ * refilling them) for as long as ctx lives and its scratch is not regrown: reserve it
+ * first with tsqs_ctx_reserve for the largest shape.  Replays and other sorts of the
+ * same ctx must not overlap on the device (they share its scratch): the calls order
+ * themselves on the ctx's completion event, direct replays are ordered by the caller.
+ * The graph belongs to ctx: release it with tsqs_graph_exec_destroy (tsqs_ctx_destroy
+ * releases any that remain).  Argument errors as tsqs_ctx_sort_segmented;
+ * TSQS_ENOMEM if scratch cannot be allocated, TSQS_ECUDA if a graph call fails. */
+int tsqs_graph_sort_segmented(tsqs_ctx *ctx, void *base, size_t nmemb_total,
+                              const uint64_t *d_seg_offsets, size_t nseg, size_t elem_size,
+                              int key_kind, void *stream, void **graph_exec);
+/* Waits for ctx's sorts, then destroys a graph made by tsqs_graph_sort_segmented on ctx
+ * (no-op for any other pointer). */
+void tsqs_graph_exec_destroy(tsqs_ctx *ctx, void *graph_exec);
+
 /* Reserves scratch for sorts up to (nmemb_total, nseg) of elem_size so that later calls
  * allocate nothing (and may run under stream capture). */
 int tsqs_ctx_reserve(tsqs_ctx *ctx, size_t nmemb_total, size_t nseg, size_t elem_size);

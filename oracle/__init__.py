@@ -12,5 +12,6 @@ from .oracle import (  # noqa: F401
     KIND_I32, KIND_U32, KIND_F32, KIND_I64, KIND_U64, KIND_F64, KIND_REC,
     PIVOT_TIERED, PIVOT_RANDOM, STATE_NAMES,
     OracleCfg, build, lib, tsqs_sort, tsqs_sort_rows, tsqs_sort_segments,
-    classical_sort, juggle_sort, median3, lower_median, three_way_split, compare, wide_sort,
+    classical_sort, juggle_sort, median3, choose_pivot, lower_median, three_way_split, compare,
+    wide_sort, std_sort_i32,
 )

@@ -18,6 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tsqs_oracle.c")
 _LIB = os.path.join(_HERE, "libtsqs_oracle.so")
+_STD_SRC = os.path.join(_HERE, "std_sort_ref.cpp")
+_STD_LIB = os.path.join(_HERE, "libstd_sort_ref.so")
 
 KIND_I32, KIND_U32, KIND_F32, KIND_I64, KIND_U64, KIND_F64, KIND_REC = 1, 2, 3, 4, 5, 6, 7
 PIVOT_TIERED, PIVOT_RANDOM = 0, 1
@@ -73,6 +75,11 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
                                "-o", tmp, _SRC, "-lpthread"])
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(_STD_LIB) or os.path.getmtime(_STD_LIB) < os.path.getmtime(_STD_SRC):
+        tmp = _STD_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-Wall", "-shared", "-fPIC",
+                               "-o", tmp, _STD_SRC])
+        os.replace(tmp, _STD_LIB)
     return _LIB
 
 
@@ -203,6 +210,23 @@ def three_way_split(a: np.ndarray, kind: int, pivot) -> tuple[np.ndarray, int, i
     lib().orc_three_way_split(a.ctypes.data, out.ctypes.data, n, kind, pv.ctypes.data,
                               ctypes.byref(nlt), ctypes.byref(neq), ctypes.byref(ngt))
     return out, nlt.value, neq.value, ngt.value
+
+
+_std_lib = None
+
+
+def std_sort_i32(a: np.ndarray) -> None:
+    """std::sort of an int32 array in place (the library reference timed beside the
+    oracle; single-threaded on the calling thread)."""
+    global _std_lib
+    if a.dtype != np.int32 or not a.flags.c_contiguous:
+        raise ValueError("std_sort_i32 takes a C-contiguous int32 array")
+    with _lock:
+        if _std_lib is None:
+            build()
+            _std_lib = ctypes.CDLL(_STD_LIB)
+            _std_lib.orc_std_sort_i32.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    _std_lib.orc_std_sort_i32(a.ctypes.data, len(a))
 
 
 def compare(x, y, kind: int) -> int:

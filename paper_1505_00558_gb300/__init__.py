@@ -199,6 +199,29 @@ class Context:
         _check(rc, "tsqs_ctx_sort_host_stream")
         return [st[i] for i in range(cnt)]
 
+    def graph_sort_segmented(self, t, offsets, graph_exec=None, *, kind: int | None = None,
+                             records: bool = False, stream=None):
+        """tsqs_graph_sort_segmented: sorts the segments of ``t`` (``offsets`` a CUDA int64
+        tensor of nseg + 1 offsets, or None for one segment) through a caller-held graph.
+        Pass the handle returned by an earlier call to update and relaunch that graph;
+        returns the handle (a cudaGraphExec_t as int, None if nothing was sorted)."""
+        kind = kind or key_kind_of(t, records)
+        p, n, es = _geom(t, kind)
+        if offsets is not None:
+            if not offsets.is_cuda or offsets.element_size() != 8 or not offsets.is_contiguous():
+                raise ValueError("offsets must be a contiguous CUDA int64 tensor")
+            po, nseg = ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1
+        else:
+            po, nseg = None, 0
+        h = ctypes.c_void_p(graph_exec)
+        _check(lib().tsqs_graph_sort_segmented(self.handle, p, n, po, nseg, es, kind,
+                                               ctypes.c_void_p(_stream_handle(stream)),
+                                               ctypes.byref(h)), "tsqs_graph_sort_segmented")
+        return h.value
+
+    def graph_destroy(self, graph_exec) -> None:
+        lib().tsqs_graph_exec_destroy(self.handle, ctypes.c_void_p(graph_exec))
+
     def sort_timed(self, t, *, kind: int | None = None, records: bool = False, stream=None,
                    max_levels: int = 256):
         """Level-by-level run of the same kernels with CUDA events around each

@@ -66,6 +66,9 @@ SIGNATURES = {
     "tsqs_ctx_destroy": (None, [_vp]),
     "tsqs_ctx_sort": (_i, [_vp, _vp, _sz, _sz, _i, _vp]),
     "tsqs_ctx_sort_segmented": (_i, [_vp, _vp, _sz, _vp, _sz, _sz, _i, _vp]),
+    "tsqs_graph_sort_segmented": (_i, [_vp, _vp, _sz, _vp, _sz, _sz, _i, _vp,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "tsqs_graph_exec_destroy": (None, [_vp, _vp]),
     "tsqs_ctx_reserve": (_i, [_vp, _sz, _sz, _sz]),
     "tsqs_ctx_scratch_bytes": (_sz, [_vp]),
     "tsqs_ctx_device_status": (_i, [_vp, _vp]),

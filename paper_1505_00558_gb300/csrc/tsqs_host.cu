@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "tsqs.h"
 #include "tsqs_internal.h"
@@ -163,6 +164,10 @@ struct tsqs_ctx {
     cudaEvent_t ev_entry = nullptr, ev_in[3] = {}, ev_sorted[3] = {}, ev_out[3] = {};
     uint32_t *d_item_status = nullptr;
     size_t item_status_cap = 0;
+    // caller-held graphs (tsqs_graph_sort_segmented): each exec with its graph, the
+    // setup node whose Job argument a later call updates, and its key kind
+    struct Held { cudaGraphExec_t exec; cudaGraph_t graph; cudaGraphNode_t setup; int kind; };
+    std::vector<Held> held;
     std::recursive_mutex mu;
 };
 
@@ -286,11 +291,10 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     return TSQS_OK;
 }
 
-int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
+// Adds the nodes of one whole sort of kind o to graph g, the first of them depending on
+// `dep` (nullptr: none).  Every kernel reads the per-call Job from c->d_job.
+int build_sort_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep) {
     const int k = o->kind;
-    if (c->exec[k]) return TSQS_OK;
-    cudaGraph_t g = nullptr;
-    CK(cudaGraphCreate(&g, 0));
     Job *pj = c->d_job;
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
@@ -302,7 +306,7 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.gridDim = dim3(c->sms * 4);
     kp.blockDim = dim3(256);
     kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_ori, g, nullptr, 0, &kp));
+    CK(cudaGraphAddKernelNode(&n_ori, g, dep, dep ? 1 : 0, &kp));
     kp.func = (void *)o->k_check;
     kp.gridDim = dim3(c->sms * 4);
     CK(cudaGraphAddKernelNode(&n_chk, g, &n_ori, 1, &kp));
@@ -429,9 +433,22 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     kp.blockDim = dim3(512);
     kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_dfin, dg, &n_dloop, 1, &kp));
+    return TSQS_OK;
+}
 
+int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
+    const int k = o->kind;
+    if (c->exec[k]) return TSQS_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    int rc = build_sort_nodes(c, o, g, nullptr);
     cudaGraphExec_t ex = nullptr;
-    CK(cudaGraphInstantiate(&ex, g, 0));
+    if (rc == TSQS_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) rc = TSQS_ECUDA;
+    if (rc) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return rc;
+    }
     c->graph[k] = g;
     c->exec[k] = ex;
     return TSQS_OK;
@@ -580,6 +597,11 @@ void tsqs_ctx_destroy(tsqs_ctx *c) {
             if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
             if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
         }
+        for (auto &h : c->held) {
+            cudaGraphExecDestroy(h.exec);
+            cudaGraphDestroy(h.graph);
+        }
+        c->held.clear();
         if (c->scratch) cudaFree(c->scratch);
         if (c->wide_rec) cudaFree(c->wide_rec);
         if (c->wide_tmp) cudaFree(c->wide_tmp);
@@ -636,6 +658,77 @@ int tsqs_ctx_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     if (!c || (nseg && !d_seg_offsets)) return TSQS_EINVAL;
     return ctx_launch(c, base, nmemb_total, d_seg_offsets, nseg, elem_size, key_kind,
                       (cudaStream_t)stream);
+}
+
+int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
+                              const uint64_t *d_seg_offsets, size_t nseg, size_t elem_size,
+                              int key_kind, void *stream, void **graph_exec) {
+    if (!c || !graph_exec || (nseg && !d_seg_offsets)) return TSQS_EINVAL;
+    int rc = validate(base, nmemb_total, elem_size, key_kind);
+    if (rc) return rc;
+    const uint64_t *offs = d_seg_offsets;
+    if (!offs && nmemb_total >= (1ull << 31)) return TSQS_EINVAL;
+    if ((offs && (nseg == 0 || nmemb_total == 0)) || (!offs && nmemb_total <= 1))
+        return TSQS_OK;                                   // nothing to sort, no graph made
+    const KindOps *o = get_ops(key_kind);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    tsqs_ctx::Held *h = nullptr;
+    if (*graph_exec) {
+        for (auto &x : c->held)
+            if ((void *)x.exec == *graph_exec) h = &x;
+        if (!h || h->kind != key_kind) return TSQS_EINVAL;     // not this ctx's, or another kind
+    }
+    if ((rc = ctx_init_device(c))) return rc;
+    if ((rc = ctx_kind_setup(c, o))) return rc;
+    if ((rc = ctx_ensure_scratch(c, nmemb_total, offs ? nseg : 1, elem_size,
+                                 part_of(o, c->plan).tile, o->leaf_max))) return rc;
+    Job j;
+    if ((rc = make_job(c, o, base, nmemb_total, offs, offs ? nseg : 1, &j))) return rc;
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args[] = {&pj, &pc, &j};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)k_setup;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    if (!h) {
+        tsqs_ctx::Held nh{};
+        nh.kind = key_kind;
+        CK(cudaGraphCreate(&nh.graph, 0));
+        rc = cudaGraphAddKernelNode(&nh.setup, nh.graph, nullptr, 0, &kp) == cudaSuccess
+                 ? build_sort_nodes(c, o, nh.graph, &nh.setup) : TSQS_ECUDA;
+        if (rc == TSQS_OK && cudaGraphInstantiate(&nh.exec, nh.graph, 0) != cudaSuccess) rc = TSQS_ECUDA;
+        if (rc) {
+            cudaGetLastError();
+            cudaGraphDestroy(nh.graph);
+            return rc;
+        }
+        c->held.push_back(nh);
+        h = &c->held.back();
+        *graph_exec = (void *)nh.exec;
+    } else {
+        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->setup, &kp));
+    }
+    if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
+    CK(cudaGraphLaunch(h->exec, s));
+    CK(cudaEventRecord(c->done_ev, s));
+    c->ev_valid = true;
+    return TSQS_OK;
+}
+
+void tsqs_graph_exec_destroy(tsqs_ctx *c, void *graph_exec) {
+    if (!c || !graph_exec) return;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    for (size_t i = 0; i < c->held.size(); i++) {
+        if ((void *)c->held[i].exec != graph_exec) continue;
+        ctx_quiesce(c);
+        cudaGraphExecDestroy(c->held[i].exec);
+        cudaGraphDestroy(c->held[i].graph);
+        c->held.erase(c->held.begin() + (long)i);
+        return;
+    }
 }
 
 int tsqs_ctx_reserve(tsqs_ctx *c, size_t nmemb_total, size_t nseg, size_t elem_size) {

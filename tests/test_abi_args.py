@@ -56,6 +56,17 @@ def test_context_and_noalloc_arguments(T, host_buf):
     assert ctx.value
     assert L.tsqs_ctx_sort(ctx, vp(p), 10, 4, T.TSQS_I64, None) == T.TSQS_EINVAL
     assert L.tsqs_ctx_sort(ctx, vp(p), 1, 4, T.TSQS_I32, None) == T.TSQS_OK
+    g = ctypes.c_void_p(None)
+    f = L.tsqs_graph_sort_segmented
+    assert f(ctx, vp(p), 10, None, 0, 4, T.TSQS_I32, None, None) == T.TSQS_EINVAL          # no handle
+    assert f(ctx, vp(p), 10, None, 0, 8, T.TSQS_I32, None, ctypes.byref(g)) == T.TSQS_EINVAL
+    assert f(ctx, vp(p), 10, None, 3, 4, T.TSQS_I32, None, ctypes.byref(g)) == T.TSQS_EINVAL  # nseg, no offsets
+    assert f(None, vp(p), 10, None, 0, 4, T.TSQS_I32, None, ctypes.byref(g)) == T.TSQS_EINVAL
+    assert f(ctx, vp(p), 1, None, 0, 4, T.TSQS_I32, None, ctypes.byref(g)) == T.TSQS_OK     # nothing to do
+    assert g.value is None
+    bogus = ctypes.c_void_p(p)                  # not a graph of this context
+    assert f(ctx, vp(p), 10, None, 0, 4, T.TSQS_I32, None, ctypes.byref(bogus)) == T.TSQS_EINVAL
+    L.tsqs_graph_exec_destroy(ctx, bogus)       # ignored
     L.tsqs_ctx_destroy(ctx)
     over = (16 << 20) // 4 + 1                     # TSQS_NOALLOC_MAX_BYTES is 16 MiB
     assert L.tsqs_sort_noalloc(vp(p), over, 4, T.TSQS_I32, None) == T.TSQS_EINVAL

@@ -1,0 +1,113 @@
+"""The depth guard against an adversarial input (Section V.B's worst case, Section V.C's
+randomised samples): tests/killer.py builds, from the sampler's seed, an int32 input
+on which the look-back-mode sort keeps one segment above the on-chip threshold at every
+level.  With the depth bound at its default (2 ceil(log2(n + 1)) + 8 levels, no debug
+override) the guard must take that segment, the output must equal the oracle's byte for
+byte, and the sort must stay within a stated multiple of a random input's time
+(marked gpu)."""
+import ctypes
+import statistics
+
+import numpy as np
+import pytest
+
+from tests.killer import killer_int32, sample_positions
+from workloads import int32_pattern
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N = 1 << 21
+SLOWDOWN_BOUND = 40.0          # killer sort time / random sort time, same size
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1505_00558_gb300 as T
+    T.lib()
+    return T
+
+
+@pytest.fixture(scope="module")
+def plan(T):
+    p = T.Plan()
+    assert T.lib().tsqs_plan_default(T.TSQS_I32, N, ctypes.byref(p)) == 0
+    p.offset_mode = 1                            # deterministic layout: the model applies
+    return p
+
+
+@pytest.fixture(scope="module")
+def killer(plan):
+    return killer_int32(N, plan.seed, plan.sample_count)
+
+
+def _median_ms(T, src, ctx, reps=3):
+    ts = []
+    for _ in range(reps + 1):
+        w = src.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        T.sort_(w, kind=T.TSQS_I32, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts[1:]), w
+
+
+def test_sampler_model_matches_pivot_kernel(T, plan, killer):
+    keys, sizes = killer
+    t = torch.from_numpy(keys.copy()).cuda()
+    L = T.lib()
+    s = torch.cuda.current_stream()
+    for m in (sizes[0], sizes[1], sizes[-1], 4097, 100_003):
+        b, e = N - m, N
+        pos = (ctypes.c_uint64 * 63)()
+        piv = ctypes.c_int32()
+        assert L.tsqs_debug_pivot(ctypes.c_void_p(t.data_ptr()), N, 4, T.TSQS_I32, b, e,
+                                  plan.sample_count, plan.seed, pos, ctypes.byref(piv),
+                                  ctypes.c_void_p(s.cuda_stream)) == 0
+        want = sample_positions(b, e, plan.sample_count, plan.seed)
+        assert [pos[k] for k in range(len(want))] == want
+
+
+def test_killer_reaches_depth_guard_and_matches_oracle(T, orc, plan, killer):
+    keys, sizes = killer
+    lg = int(np.ceil(np.log2(N + 1)))
+    assert len(sizes) == 2 * lg + 8                   # the model keeps the segment up
+    ctx = T.Context(plan)
+    src = torch.from_numpy(keys.copy()).cuda()
+    ms_k, out = _median_ms(T, src, ctx)
+    assert ctx.status() == T.TSQS_OK
+    st = ctx.stats()
+    # the segment went to the depth guard's bitonic fallback (no debug override)
+    assert st["deep_sorted_keys"] >= sizes[-1] - 64
+    assert st["levels"] >= 2 * lg + 7
+    exp = keys.copy()
+    orc.tsqs_sort(exp, orc.KIND_I32)
+    assert out.cpu().numpy().tobytes() == exp.tobytes()
+    # bounded time: the guard's O(n log^2 n) fallback after the deep levels
+    rnd = torch.from_numpy(int32_pattern("random", N, seed=5)).cuda()
+    ms_r, _ = _median_ms(T, rnd, ctx)
+    print(f"killer {ms_k:.3f} ms, random {ms_r:.3f} ms, ratio {ms_k / ms_r:.1f}, levels "
+          f"{st['levels']}, deep keys {st['deep_sorted_keys']}")
+    assert ms_k <= SLOWDOWN_BOUND * ms_r
+    ctx.close()
+
+
+def test_killer_in_default_reservation_mode_is_sorted(T, orc, killer):
+    """In the default (atomic-cursor) mode the tiles' runs land in arrival order, which
+    the adversary cannot model; the sort is still exact."""
+    keys, _ = killer
+    ctx = T.Context()
+    src = torch.from_numpy(keys.copy()).cuda()
+    T.sort_(src, kind=T.TSQS_I32, ctx=ctx)
+    assert ctx.status() == T.TSQS_OK
+    st = ctx.stats()
+    print(f"default mode: levels {st['levels']}, deep keys {st['deep_sorted_keys']}")
+    exp = keys.copy()
+    orc.tsqs_sort(exp, orc.KIND_I32)
+    assert src.cpu().numpy().tobytes() == exp.tobytes()
+    ctx.close()
