@@ -1247,6 +1247,148 @@ __device__ __forceinline__ void bitonic_mirror(C *s, uint32_t P, uint32_t len) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------------
+// Items of 513 .. 4096 elements: 32 keys per thread, P = 1024, 2048 or 4096.  Lane l of
+// warp w holds v[r] = element w*1024 + l*32 + r ("rows").  The network is bitonic: each
+// merge of width k = 2^K takes two sorted halves and compares i with i ^ (k - 1), then
+// runs the half-cleaners k/4 .. 1, with the minimum to the lower index (the mirror form,
+// as in bitonic_mirror).  Every compare-exchange is between two registers of one thread:
+//   - strides 16 .. 1 in rows;
+//   - for k <= 1024, the mirror stage and strides k/4 .. 32 in "columns" (lane l' holds
+//     in register q element q*32 + l'), reached by a warp-local transpose through the
+//     warp's 32 x 33 region of the block buffer (element (a, b) at w*1056 + a*33 + b:
+//     both directions touch 32 distinct banks) that writes the upper half of each k-block
+//     reversed (its lanes store row l ^ (k/64 - 1), column 31 - r): the mirror stage is
+//     then the half-cleaner of stride k/2, a register pair as well;
+//   - for k = 2048 and 4096 the mirror stage (and the stride 1024) cross warps: each
+//     thread reads its element and the partner's from the block buffer and keeps its
+//     side, then strides 512 .. 32 run in columns.
+// One copy of the code serves every merge width (a loop over K), so the kernel's
+// instructions stay in the instruction cache.  Warps holding only padding (the largest
+// key) skip the network: the padding sits at the top and never moves, and reads of their
+// regions take the largest key instead.
+// ---------------------------------------------------------------------------------
+
+template <class C>
+__device__ __forceinline__ void rows_cleaners(C (&v)[32]) {
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+#pragma unroll
+        for (int r = 0; r < 32; r++)
+            if ((r & j) == 0) cx(v[r], v[r | j]);
+    }
+}
+
+// Sorts the item held in rows by warps 0 .. P/1024 - 1 (warps nact and above hold only
+// padding); s is the block buffer (32 x 33 elements per warp).  Every thread of the
+// block calls it (block barriers when P > 1024).  Leaves the sorted item in rows.
+template <class C>
+__device__ __forceinline__ void sort_item32(C (&v)[32], C *s, uint32_t P, uint32_t nact) {
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const bool act = w < nact;
+    C *wb = s + w * 1056u;
+    if (act) {                                   // merges of width 2 .. 32 in registers
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int r = 0; r < 32; r++) {
+                const int q = r ^ (k - 1);
+                if (q > r) cx(v[r], v[q]);
+            }
+#pragma unroll
+            for (int j = k >> 2; j >= 1; j >>= 1) {
+#pragma unroll
+                for (int r = 0; r < 32; r++)
+                    if ((r & j) == 0) cx(v[r], v[r | j]);
+            }
+        }
+    }
+#pragma unroll 1
+    for (uint32_t K = 6; (1u << K) <= P; K++) {
+        uint32_t lim;                            // largest column stride left, in rows
+        if (K <= 10u) {
+            lim = 1u << (K - 6);
+            if (act) {
+                __syncwarp();                    // every lane has read its row
+                if (lane & lim) {                // upper half: reversed
+                    C *b = wb + (lane ^ (lim - 1u)) * 33u + 31u;
+#pragma unroll
+                    for (int r = 0; r < 32; r++) b[-r] = v[r];
+                } else {
+                    C *b = wb + lane * 33u;
+#pragma unroll
+                    for (int r = 0; r < 32; r++) b[r] = v[r];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 32; q++) v[q] = wb[q * 33u + lane];
+            }
+        } else {
+            // k = 2048 or 4096: the mirror stage i vs i ^ (k - 1) reads the partner from
+            // warp w ^ (k/1024 - 1) with row and column reversed (no data moves, so the
+            // regions of padding warps keep meaning the largest key); this thread keeps
+            // the side of its element in columns
+            lim = 16u;
+            __syncthreads();                                 // all reads of the buffer done
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < 32; r++) wb[lane * 33u + r] = v[r];
+            }
+            __syncthreads();
+            if (act) {
+                const uint32_t half = 1u << (K - 11);        // warp bit of the upper half
+                const uint32_t pw = w ^ (2u * half - 1u);
+                const bool lower = (w & half) == 0u, pact = pw < nact;
+                const C *pb = s + pw * 1056u + (31u - lane);
+#pragma unroll
+                for (int q = 0; q < 32; q++) {
+                    const C part = pact ? pb[(31 - q) * 33] : c_max<C>();
+                    v[q] = cx_side(wb[q * 33u + lane], part, lower);
+                    if ((q & 7) == 7) asm volatile("" ::: "memory");   // loads in groups of 8
+                }
+            }
+            if (K == 12u) {                                  // stride 1024: warp w ^ 1
+                __syncthreads();
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < 32; q++) wb[q * 33u + lane] = v[q];
+                }
+                __syncthreads();
+                if (act) {
+                    const uint32_t pw = w ^ 1u;
+                    const bool lower = (w & 1u) == 0u, pact = pw < nact;
+                    const C *pb = s + pw * 1056u + lane;
+#pragma unroll
+                    for (int q = 0; q < 32; q++) {
+                        const C part = pact ? pb[q * 33] : c_max<C>();
+                        v[q] = cx_side(v[q], part, lower);
+                        if ((q & 7) == 7) asm volatile("" ::: "memory");
+                    }
+                }
+            }
+            __syncthreads();                                 // partner reads done
+        }
+        if (act) {
+            // column strides lim*32 .. 32 in registers
+#pragma unroll
+            for (int js = 16; js >= 1; js >>= 1) {
+                if ((uint32_t)js <= lim) {
+#pragma unroll
+                    for (int q = 0; q < 32; q++)
+                        if ((q & js) == 0) cx(v[q], v[q | js]);
+                }
+            }
+            // columns -> rows (each lane rewrites the words it read), strides 16 .. 1
+#pragma unroll
+            for (int q = 0; q < 32; q++) wb[q * 33u + lane] = v[q];
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 32; r++) v[r] = wb[lane * 33u + r];
+            rows_cleaners(v);
+        }
+    }
+}
+
 // Shared-memory layout of the leaf kernel: the padded sort buffer, then the raw
 // prefetch slot (the next item's 16-byte-aligned hull) and its mbarrier.
 template <int KIND>
@@ -1275,9 +1417,6 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     C *s = reinterpret_cast<C *>(leaf_raw);
     S *pre = reinterpret_cast<S *>(leaf_raw + LY::off_pre);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(leaf_raw + LY::off_bar);
-    __shared__ LeafItem s_it[LY::NSLOT];
-    __shared__ int64_t s_cs[LY::NSLOT], s_ce[LY::NSLOT];
-    __shared__ uint32_t s_ok[LY::NSLOT];
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
     // Leaf items queue up across levels (their ranges are never touched by a later
     // partition); a level's pass runs only when the queue would otherwise outgrow its
@@ -1286,75 +1425,124 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     const uint32_t nl = min(ctl->nleaf, job->cap_leaves);
     if (!final_pass && nl <= job->leaf_defer) return;
     S *out = reinterpret_cast<S *>(job->out);
-    const int64_t n = (int64_t)job->n;
-    const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
-    const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
     const uint32_t wait_limit = 1u << 20;
+    // per-block totals, kept by thread 0 in shared memory (registers stay free for keys)
+    __shared__ unsigned long long s_sorted, s_filled, s_items;
+    // Claimed items, two deep: the item being sorted and the next one, whose hull is
+    // copied into the prefetch slot as soon as the current keys have left it.  Claiming
+    // (the queue read and the hull arithmetic) happens after an item is written out, when
+    // no keys are held in registers; issuing the copy takes a few words from here.
+    struct Meta { LeafItem it; int64_t cs, ce; const S *from; uint32_t bytes, ok; };
+    __shared__ Meta s_meta[2];
 
-    // thread 0: claim the next item into `slot` and start the bulk copy of its hull
-    auto claim = [&](int slot) {
+    // thread 0: claim the next item into s_meta[m] (no copy yet)
+    auto prepare = [&](int m) {
+        Meta &d = s_meta[m];
         const uint32_t ii = atomicAdd(&ctl->leaf_claim, 1u);
-        if (ii >= nl) { s_ok[slot] = 0u; return; }
+        d.ok = ii < nl ? 1u : 0u;
+        d.cs = d.ce = 0;
+        d.bytes = 0;
+        if (!d.ok) return;
         const LeafItem it = job->leaves[ii];
-        s_it[slot] = it;
-        s_ok[slot] = 1u;
-        s_cs[slot] = s_ce[slot] = 0;
+        d.it = it;
         if ((it.kind & 0xFFu) == LEAF_SORT && it.len <= (uint32_t)kMaxSmall) {
+            const int64_t n = (int64_t)job->n;
+            const int64_t e_lo = (int64_t)((V - (int64_t)job->vec_off % V) % V);
+            const int64_t e_hi = n - ((n + (int64_t)job->vec_off) % V);
             const S *src = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0);
             const int64_t b = (int64_t)it.begin, e = b + it.len;
             const int64_t cs = max(b - ((b + (int64_t)job->vec_off) % V), e_lo);
             const int64_t ce = min(e + ((V - ((e + (int64_t)job->vec_off) % V)) % V), e_hi);
             if (ce > cs) {
-                s_cs[slot] = cs;
-                s_ce[slot] = ce;
-                const uint32_t bytes = (uint32_t)((ce - cs) * (int64_t)sizeof(S));
-                mbar_arrive_tx(&bar[slot], bytes);
-                tma_load_1d(pre + (size_t)slot * LY::PRE, src + cs, bytes, &bar[slot]);
+                d.cs = cs;
+                d.ce = ce;
+                d.from = src + cs;
+                d.bytes = (uint32_t)((ce - cs) * (int64_t)sizeof(S));
             }
+        }
+    };
+    // thread 0: start the bulk copy of s_meta[m]'s hull into the prefetch slot
+    auto issue = [&](int m) {
+        const uint32_t bytes = s_meta[m].bytes;
+        if (s_meta[m].ok && bytes) {
+            mbar_arrive_tx(&bar[0], bytes);
+            tma_load_1d(pre, s_meta[m].from, bytes, &bar[0]);
         }
     };
 
     if (threadIdx.x == 0) {
-        for (int b = 0; b < LY::NSLOT; b++) mbar_init(&bar[b], 1);
+        mbar_init(&bar[0], 1);
         fence_mbar_init();
-        claim(0);
+        s_sorted = s_filled = s_items = 0ull;
+        prepare(0);
+        issue(0);
+        prepare(1);
     }
     __syncthreads();
-    uint32_t phase[LY::NSLOT] = {};
-    uint64_t sorted = 0, filled = 0, items = 0;
+    uint32_t phase = 0;
     for (uint32_t iter = 0;; iter++) {
-        const int sl = 0;                                 // the one prefetch slot
-        if (!s_ok[sl]) break;
-        const LeafItem it = s_it[sl];
-        const int64_t cs = s_cs[sl], ce = s_ce[sl];
-        items++;
+        const int cur = (int)(iter & 1u);
+        if (!s_meta[cur].ok) break;
+        const LeafItem it = s_meta[cur].it;
+        const int64_t cs = s_meta[cur].cs, ce = s_meta[cur].ce;
+        if (threadIdx.x == 0) s_items++;
         const bool is_fill = (it.kind & 0xFFu) == LEAF_FILL;
         const bool is_sort = !is_fill && it.len <= (uint32_t)kMaxSmall;
         const S *src = buffer<K>(job, (it.kind & kLeafInAlt) ? 1 : 0);   // may equal out
         uint32_t P = 32;
+        // items above 512 elements: 32 keys per thread in registers (sort_item32)
+        const bool wide = MAXE == 32 && is_sort && it.len > 512u;
+        const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+        C v[32];
         if (is_sort) {
             if (ce > cs) {
-                if (!mbar_wait(&bar[sl], phase[sl], wait_limit)) {
+                if (!mbar_wait(&bar[0], phase, wait_limit)) {
                     if (threadIdx.x == 0) set_status(ctl, TSQS_ETIMEOUT);
-                    mbar_wait(&bar[sl], phase[sl], wait_limit);   // let the copy land
+                    mbar_wait(&bar[0], phase, wait_limit);        // let the copy land
                 }
-                phase[sl] ^= 1u;
+                phase ^= 1u;
             }
-            const S *slot = pre + (size_t)sl * LY::PRE;
+            const S *slot = pre;
             while (P < it.len) P <<= 1;
-#pragma unroll 4
-            for (uint32_t i = threadIdx.x; i < P; i += LB) {
-                C c = c_max<C>();
-                if (i < it.len) {
-                    const int64_t e = (int64_t)it.begin + i;
-                    c = K::canon((e >= cs && e < ce) ? slot[e - cs] : src[e]);
+            if (wide) {
+                // straight from the prefetch slot into registers: lane l of warp w takes
+                // elements w*1024 + q*32 + l (the input order does not matter to the
+                // network, so they serve as its rows); padding is the largest key
+                if (w * 1024u < it.len) {
+                    const int64_t b = (int64_t)it.begin;
+                    const uint32_t i0 = w * 1024u + lane;
+                    if (cs <= b && b + (int64_t)it.len <= ce && (w + 1u) * 1024u <= it.len) {
+                        const S *sp = slot + (b - cs) + i0;
+#pragma unroll
+                        for (int q = 0; q < 32; q++) v[q] = K::canon(sp[q * 32]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; q++) {
+                            const uint32_t i = i0 + 32u * q;
+                            C c = c_max<C>();
+                            if (i < it.len) {
+                                const int64_t e = b + i;
+                                c = K::canon((e >= cs && e < ce) ? slot[e - cs] : src[e]);
+                            }
+                            v[q] = c;
+                        }
+                    }
                 }
-                s[padc<C>(i)] = c;
+            } else {
+#pragma unroll 4
+                for (uint32_t i = threadIdx.x; i < P; i += LB) {
+                    C c = c_max<C>();
+                    if (i < it.len) {
+                        const int64_t e = (int64_t)it.begin + i;
+                        c = K::canon((e >= cs && e < ce) ? slot[e - cs] : src[e]);
+                    }
+                    s[padc<C>(i)] = c;
+                }
             }
         }
         fence_proxy_async();                // this slot's reads precede its next bulk copy
-        __syncthreads();                    // sort buffer loaded, slot free, s_it read
-        if (threadIdx.x == 0) claim(0);                   // prefetch the next item meanwhile
+        __syncthreads();                    // keys loaded, slot free, s_meta[cur] read
+        if (threadIdx.x == 0) issue(cur ^ 1);             // prefetch the next item meanwhile
         if (is_fill) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
             S rep[V];
@@ -1367,27 +1555,51 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             if (threadIdx.x < head) out[x + threadIdx.x] = val;
             for (uint32_t q = threadIdx.x; q < nvec; q += LB) stg_vec<S, V>(out + x + head + q * V, rep);
             for (uint32_t i = body_end + threadIdx.x; i < it.len; i += LB) out[x + i] = val;
-            filled += it.len;
+            if (threadIdx.x == 0) s_filled += it.len;
         } else if (!is_sort) {
             if (threadIdx.x == 0) set_status(ctl, TSQS_EINTERNAL);
+        } else if (wide) {
+            const uint32_t nact = (it.len + 1023u) / 1024u;
+            sort_item32<C>(v, s, P, nact);
+            // rows -> columns through the warp's region, then stores of 32 consecutive
+            // elements per warp instruction
+            if (w < nact) {
+                C *wb = s + w * 1056u;
+#pragma unroll
+                for (int r = 0; r < 32; r++) wb[lane * 33u + r] = v[r];
+                __syncwarp();
+                S *op = out + it.begin + w * 1024u + lane;
+                if ((w + 1u) * 1024u <= it.len) {
+#pragma unroll
+                    for (int q = 0; q < 32; q++) op[q * 32] = K::uncanon(wb[q * 33u + lane]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; q++)
+                        if (w * 1024u + 32u * q + lane < it.len) op[q * 32] = K::uncanon(wb[q * 33u + lane]);
+                }
+            }
+            if (threadIdx.x == 0) s_sorted += it.len;
         } else {
-            // E = min(MAXE, P / 32) keys per thread
-            const uint32_t E = min((uint32_t)MAXE, P / 32u);
+            // E = min(MAXE, P / 32) keys per thread; with the 32-key path for items
+            // above 512, at most 8 here (two warps for P = 512)
+            constexpr uint32_t EMAX = MAXE == 32 ? 8u : (uint32_t)MAXE;
+            const uint32_t E = min(EMAX, P / 32u);
             if (E == 1) bitonic_mirror<C, 1>(s, P, it.len);
             else if (E == 2) bitonic_mirror<C, 2>(s, P, it.len);
             else if (E == 4) bitonic_mirror<C, 4>(s, P, it.len);
-            else if (E == 8) bitonic_mirror<C, (MAXE >= 8 ? 8 : 1)>(s, P, it.len);
-            else if (E == 16) bitonic_mirror<C, (MAXE >= 16 ? 16 : 1)>(s, P, it.len);
-            else bitonic_mirror<C, (MAXE >= 32 ? 32 : 1)>(s, P, it.len);
+            else if (E == 8) bitonic_mirror<C, (EMAX >= 8 ? 8 : 1)>(s, P, it.len);
+            else if (E == 16) bitonic_mirror<C, (EMAX >= 16 ? 16 : 1)>(s, P, it.len);
+            else bitonic_mirror<C, (EMAX >= 32 ? 32 : 1)>(s, P, it.len);
             for (uint32_t i = threadIdx.x; i < it.len; i += LB) out[it.begin + i] = K::uncanon(s[padc<C>(i)]);
-            sorted += it.len;
+            if (threadIdx.x == 0) s_sorted += it.len;
         }
+        if (threadIdx.x == 0) prepare(cur);              // the item after the next one
         __syncthreads();                    // sort buffer free, next item's meta visible
     }
-    if (threadIdx.x == 0 && items) {
-        atomicAdd((unsigned long long *)&ctl->leaf_sorted, (unsigned long long)sorted);
-        atomicAdd((unsigned long long *)&ctl->leaf_filled, (unsigned long long)filled);
-        atomicAdd((unsigned long long *)&ctl->leaf_items, (unsigned long long)items);
+    if (threadIdx.x == 0 && s_items) {
+        atomicAdd((unsigned long long *)&ctl->leaf_sorted, s_sorted);
+        atomicAdd((unsigned long long *)&ctl->leaf_filled, s_filled);
+        atomicAdd((unsigned long long *)&ctl->leaf_items, s_items);
     }
     // the last block to finish empties the queue (every block has read nleaf and made
     // its last claim by then)

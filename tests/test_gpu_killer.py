@@ -32,10 +32,16 @@ def T():
 
 @pytest.fixture(scope="module")
 def plan(T):
+    # the built-in shape (zero fields take the defaults: 192 x 24 partition tiles, on-chip
+    # threshold 4096, 31 samples), not a plan an autotuner may have cached in this process;
+    # look-back offsets give the deterministic layout the model follows
     p = T.Plan()
-    assert T.lib().tsqs_plan_default(T.TSQS_I32, N, ctypes.byref(p)) == 0
-    p.offset_mode = 1                            # deterministic layout: the model applies
-    return p
+    p.offset_mode = 1
+    ctx = T.Context(p)
+    full = ctx.plan()
+    ctx.close()
+    assert (full.tile_items, full.small_threshold, full.sample_count) == (0, 4096, 31)
+    return full
 
 
 @pytest.fixture(scope="module")
