@@ -42,10 +42,10 @@ FALLBACK_HBM_GBS = 6800.0
 # from an ncu capture of the kernel source with this sha256 prefix (null when the
 # kernel changed since).
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-width k_partition launch at the
-# headline size (2^27 int32, level 3 of an instrumented sort): 537.0 MB + 480.1 MB for
+# headline size (2^27 int32, level 3 of an instrumented sort): 537.1 MB + 479.1 MB for
 # 134,217,721 keys; valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"kernels_sha": "434d460783c85398",
-               "bytes_per_key": (537138944 + 479178496) / 134217721,
+NCU_TRAFFIC = {"kernels_sha": "49e5e1e39b52f7c1",
+               "bytes_per_key": (537055488 + 479089920) / 134217721,
                "source": "profiles/k_partition_2e27_int32_traffic.md"}
 
 
