@@ -4,7 +4,7 @@
 namespace tsqs {
 
 namespace {
-constexpr int kLeafBlock = 512, kLeafMaxE = 8, kPivotBlock = 256;
+constexpr int kLeafBlock = 256, kLeafMaxE = 16, kPivotBlock = 256;
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
 PartVariant part_variant() {
@@ -39,7 +39,7 @@ KindOps make_ops() {
     o.k_deep_stage = (const void *)k_deep_stage<KIND>;
     o.k_deep_finish = (const void *)k_deep_finish<KIND>;
     o.deep_smem = (int)((kDeepTile + kDeepTile / kPadGroup<typename Key<KIND>::C>) * sizeof(typename Key<KIND>::C));
-    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 1>;
+    o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 2>;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;

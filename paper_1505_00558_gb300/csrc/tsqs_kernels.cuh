@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tsqs_internal.h"
 #include "tsqs.h"
 
@@ -1389,12 +1391,58 @@ __device__ __forceinline__ void sort_item32(C (&v)[32], C *s, uint32_t P, uint32
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Records (16-byte {key, payload}, ordered by (key, payload)) in the leaf pass.  A
+// 128-bit compare-exchange costs about three times a 64-bit one, so an item is sorted by
+// 64-bit packed keys: ((key - min key) >> sh) << 12 | index in the item, sh the bits the
+// item's key range has beyond 52.  The packed order is the record order except among
+// records whose shifted keys are equal (equal keys, or keys that differ only in the sh
+// dropped bits): such runs are then put in (key, payload) order from the records
+// themselves.  Runs are short on ordinary inputs; an item with a run longer than 32
+// is sorted once more by an indirect network that compares whole records.
+// ---------------------------------------------------------------------------------
+
+constexpr unsigned long long kPackNone = ~0ull;            // padding: above every packed key
+
+__device__ __forceinline__ U128 rec_canon(const Rec16 &r) { return U128{r.pay, r.key}; }
+
+// Indirect bitonic sort of the packed entries s[0, P) (padded layout) by the records they
+// index, src[base + (x & 0xFFF)]; padding entries (index >= len) sort last.  Every thread
+// of the block calls it.
+template <int LB>
+__device__ void rec_sort_indirect(unsigned long long *s, uint32_t P, uint32_t len, const Rec16 *src,
+                                  uint64_t base) {
+    using C64 = unsigned long long;
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j >= 1; j >>= 1) {
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < P; i += LB) {
+                const uint32_t q = i ^ j;
+                if (q <= i) continue;
+                const C64 a = s[padc<C64>(i)], b = s[padc<C64>(q)];
+                const uint32_t ia = (uint32_t)(a & 0xFFFu), ib = (uint32_t)(b & 0xFFFu);
+                bool gt;                                     // record(a) > record(b)
+                if (ia >= len || ib >= len) gt = ia >= len && ib < len;
+                else gt = c_lt(rec_canon(src[base + ib]), rec_canon(src[base + ia]));
+                const bool up = (i & k) == 0u;
+                if (gt == up) {
+                    s[padc<C64>(i)] = b;
+                    s[padc<C64>(q)] = a;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // Shared-memory layout of the leaf kernel: the padded sort buffer, then the raw
 // prefetch slot (the next item's 16-byte-aligned hull) and its mbarrier.
 template <int KIND>
 struct LeafLayout {
     using S = typename Key<KIND>::S;
-    using C = typename Key<KIND>::C;
+    // the sort buffer holds the canonical keys, for records the packed 64-bit sort keys
+    using C = typename std::conditional<KIND == TSQS_U64_U64_REC, unsigned long long,
+                                        typename Key<KIND>::C>::type;
     static constexpr int PRE = kMaxSmall + 2 * Key<KIND>::V;          // elements per slot
     static constexpr size_t sort_bytes = ((kMaxSmall + kMaxSmall / kPadGroup<C>) * sizeof(C) + 127) / 128 * 128;
     static constexpr size_t off_pre = sort_bytes;
@@ -1415,6 +1463,9 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
     static_assert(LB * MAXE >= kMaxSmall, "block too small for the largest leaf");
     extern __shared__ __align__(128) unsigned char leaf_raw[];
     C *s = reinterpret_cast<C *>(leaf_raw);
+    unsigned long long *sp64 = reinterpret_cast<unsigned long long *>(leaf_raw);   // records
+    __shared__ unsigned long long s_kmin[LB / 32], s_kmax[LB / 32];
+    __shared__ uint32_t s_sh;
     S *pre = reinterpret_cast<S *>(leaf_raw + LY::off_pre);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(leaf_raw + LY::off_bar);
     if (block_aborted(ctl)) return;                         // queues may be inconsistent
@@ -1504,7 +1555,49 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             }
             const S *slot = pre;
             while (P < it.len) P <<= 1;
-            if (wide) {
+            if constexpr (KIND == TSQS_U64_U64_REC) {
+                // packed keys: the item's key range first (block min / max), then
+                // ((key - min) >> sh) << 12 | index, padding above every packed key
+                constexpr int RQ = (kMaxSmall + LB - 1) / LB;
+                unsigned long long kv[RQ];
+                unsigned long long lo = ~0ull, hi = 0ull;
+                const int64_t b = (int64_t)it.begin;
+#pragma unroll
+                for (int q = 0; q < RQ; q++) {
+                    const uint32_t i = threadIdx.x + (uint32_t)(q * LB);
+                    kv[q] = 0ull;
+                    if (i < it.len) {
+                        const int64_t e = b + i;
+                        kv[q] = ((e >= cs && e < ce) ? slot[e - cs] : src[e]).key;
+                        lo = min(lo, kv[q]);
+                        hi = max(hi, kv[q]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, (unsigned long long)__shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, (unsigned long long)__shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if ((threadIdx.x & 31u) == 0u) { s_kmin[threadIdx.x >> 5] = lo; s_kmax[threadIdx.x >> 5] = hi; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int q = 1; q < LB / 32; q++) { lo = min(lo, s_kmin[q]); hi = max(hi, s_kmax[q]); }
+                    const unsigned long long range = hi - lo;
+                    const uint32_t bits = range ? 64u - (uint32_t)__clzll((long long)range) : 0u;
+                    s_sh = bits > 52u ? bits - 52u : 0u;
+                    s_kmin[0] = lo;
+                }
+                __syncthreads();
+                const unsigned long long kmin = s_kmin[0];
+                const uint32_t sh = s_sh;
+#pragma unroll
+                for (int q = 0; q < RQ; q++) {
+                    const uint32_t i = threadIdx.x + (uint32_t)(q * LB);
+                    if (i < P)
+                        sp64[padc<unsigned long long>(i)] =
+                            i < it.len ? (((kv[q] - kmin) >> sh) << 12) | i : kPackNone;
+                }
+            } else if (wide) {
                 // straight from the prefetch slot into registers: lane l of warp w takes
                 // elements w*1024 + q*32 + l (the input order does not matter to the
                 // network, so they serve as its rows); padding is the largest key
@@ -1528,7 +1621,7 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
                         }
                     }
                 }
-            } else {
+            } else if constexpr (KIND != TSQS_U64_U64_REC) {
 #pragma unroll 4
                 for (uint32_t i = threadIdx.x; i < P; i += LB) {
                     C c = c_max<C>();
@@ -1540,9 +1633,12 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
                 }
             }
         }
+        // records keep the slot until they are written out (the output is gathered from
+        // it); every other item has left it
+        const bool hold_slot = KIND == TSQS_U64_U64_REC && is_sort;
         fence_proxy_async();                // this slot's reads precede its next bulk copy
         __syncthreads();                    // keys loaded, slot free, s_meta[cur] read
-        if (threadIdx.x == 0) issue(cur ^ 1);             // prefetch the next item meanwhile
+        if (threadIdx.x == 0 && !hold_slot) issue(cur ^ 1);   // prefetch the next item meanwhile
         if (is_fill) {
             const S val = K::uncanon(c_from<C>(it.v_lo, it.v_hi));
             S rep[V];
@@ -1558,6 +1654,55 @@ __global__ void __launch_bounds__(LB, MINB) k_leaf(const Job *__restrict__ job, 
             if (threadIdx.x == 0) s_filled += it.len;
         } else if (!is_sort) {
             if (threadIdx.x == 0) set_status(ctl, TSQS_EINTERNAL);
+        } else if constexpr (KIND == TSQS_U64_U64_REC) {
+            using C64 = unsigned long long;
+            // the item's records, in the prefetch slot (16-byte elements: the hull is the
+            // item itself)
+            const Rec16 *rsrc = reinterpret_cast<const Rec16 *>(pre) - cs;
+            const uint32_t E = min((uint32_t)MAXE, P / 32u);
+            if (E == 1) bitonic_mirror<C64, 1>(sp64, P, it.len);
+            else if (E == 2) bitonic_mirror<C64, 2>(sp64, P, it.len);
+            else if (E == 4) bitonic_mirror<C64, 4>(sp64, P, it.len);
+            else if (E == 8) bitonic_mirror<C64, (MAXE >= 8 ? 8 : 1)>(sp64, P, it.len);
+            else bitonic_mirror<C64, (MAXE >= 16 ? 16 : 1)>(sp64, P, it.len);
+            // runs of equal shifted keys: a run longer than 32 sends the item to the
+            // indirect network; shorter ones are put in record order by their first thread
+            bool longrun = false;
+            for (uint32_t j = threadIdx.x; j + 32u < it.len; j += LB)
+                longrun |= (sp64[padc<C64>(j)] >> 12) == (sp64[padc<C64>(j + 32u)] >> 12);
+            if (__syncthreads_or(longrun)) {
+                rec_sort_indirect<LB>(sp64, P, it.len, rsrc, it.begin);
+            } else {
+                for (uint32_t j = threadIdx.x; j + 1u < it.len; j += LB) {
+                    const C64 h = sp64[padc<C64>(j)] >> 12;
+                    if ((j > 0u && (sp64[padc<C64>(j - 1u)] >> 12) == h) ||
+                        (sp64[padc<C64>(j + 1u)] >> 12) != h) continue;
+                    uint32_t e = j + 1u;                         // run [j, e)
+                    while (e < it.len && (sp64[padc<C64>(e)] >> 12) == h) e++;
+                    for (uint32_t a = j + 1u; a < e; a++) {      // insertion by (key, payload)
+                        const C64 x = sp64[padc<C64>(a)];
+                        const U128 xv = rec_canon(rsrc[it.begin + (x & 0xFFFu)]);
+                        uint32_t c = a;
+                        while (c > j) {
+                            const C64 y = sp64[padc<C64>(c - 1u)];
+                            if (!c_lt(xv, rec_canon(rsrc[it.begin + (y & 0xFFFu)]))) break;
+                            sp64[padc<C64>(c)] = y;
+                            c--;
+                        }
+                        sp64[padc<C64>(c)] = x;
+                    }
+                }
+                __syncthreads();
+            }
+            // write out in order, gathered from the slot (a copy: the output may be the
+            // records' own buffer), then release the slot to the next item's copy
+            Rec16 *rout = reinterpret_cast<Rec16 *>(out);
+            for (uint32_t j = threadIdx.x; j < it.len; j += LB)
+                rout[it.begin + j] = rsrc[it.begin + (sp64[padc<C64>(j)] & 0xFFFu)];
+            if (threadIdx.x == 0) s_sorted += it.len;
+            fence_proxy_async();
+            __syncthreads();
+            if (threadIdx.x == 0) issue(cur ^ 1);
         } else if (wide) {
             const uint32_t nact = (it.len + 1023u) / 1024u;
             sort_item32<C>(v, s, P, nact);
