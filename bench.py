@@ -44,8 +44,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-width k_partition launch at the
 # headline size (2^27 int32, level 3 of an instrumented sort): 537.1 MB + 479.1 MB for
 # 134,217,721 keys; valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"kernels_sha": "49e5e1e39b52f7c1",
-               "bytes_per_key": (537055488 + 479089920) / 134217721,
+NCU_TRAFFIC = {"kernels_sha": "a17c6560a5a696a7",
+               "bytes_per_key": (537057024 + 478985472) / 134217721,
                "source": "profiles/k_partition_2e27_int32_traffic.md"}
 
 
