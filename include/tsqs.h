@@ -78,7 +78,17 @@ typedef struct {
                                       cursor (default; tiles never wait on each other),
                                   1 = decoupled look-back over (#<p, #>p) in tile order
                                       (deterministic intermediate layout)              */
-    int32_t  pad;
+    int32_t  schedule;         /* order of the partition steps:
+                                  0 = by size (default): inputs of at most 2^24
+                                      elements run task-parallel, larger ones level by
+                                      level,
+                                  1 = level by level: one launch of each step per level
+                                      of the recursion, every segment of a level at once,
+                                  2 = task-parallel at any size: one persistent launch
+                                      in which each segment is partitioned as soon as
+                                      its parent is done, with no level barrier.
+                                  Look-back offsets (offset_mode 1) always run level by
+                                  level.                                                */
     uint64_t seed;             /* seed of the jittered sample positions (Section V.C)   */
 } tsqs_plan;
 
@@ -258,11 +268,14 @@ size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
 int tsqs_plan_default(int key_kind, size_t n_hint, tsqs_plan *out);
 
 /* ---------------------------------------------------------------------------------
- * Instrumented level-by-level run (for measurement): the same kernels launched one at
- * a time from the host, with a CUDA event recorded around every partition launch.
- * Synchronises `stream`.  Writes up to max_levels partition-kernel durations (ms) to
- * h_ms and the keys each of those launches read to h_keys; returns the number of
- * levels through *levels.
+ * Instrumented run (for measurement): the same kernels as the context's graph for this
+ * size, launched one at a time from the host.  Synchronises `stream`.
+ * Level-by-level schedule: a CUDA event pair around every partition launch; writes up
+ * to max_levels partition-kernel durations (ms) to h_ms, the keys each of those
+ * launches read to h_keys and each level's leaf-launch duration to h_leaf_ms; returns
+ * the number of levels through *levels.
+ * Task-parallel schedule (plan.schedule, size): one entry: the task kernel's duration,
+ * the keys it partitioned over all depths, and the leaf pass's duration; *levels = 1.
  * ------------------------------------------------------------------------------- */
 int tsqs_ctx_sort_timed(tsqs_ctx *ctx, void *base, size_t nmemb, size_t elem_size,
                         int key_kind, void *stream, float *h_ms, uint64_t *h_keys,
@@ -315,10 +328,13 @@ void tsqs_debug_set_deep_level(uint32_t level);
  * loop on ordinary inputs.  0 restores the default. */
 void tsqs_debug_set_leaf_defer(uint32_t items);
 
-/* When on != 0, partition tile 1 of every later level of the default context never
- * publishes its look-back word, so the waits of its successors must run into the
- * spin limit and the sort must end with TSQS_ETIMEOUT (a host-side fault injection
- * that neither faults nor hangs the device).  0 restores normal operation. */
+/* When on == 1, partition tile 1 of every later level-by-level sort never publishes
+ * its look-back word, so the waits of its successors must run into the spin limit and
+ * the sort must end with TSQS_ETIMEOUT.  When on == 2, the first segment of every later
+ * task-parallel sort never publishes its tile rows, so every block that claimed one of
+ * its tiles must run into the spin limit, with the same result.  Both are host-side
+ * fault injections that neither fault nor hang the device.  0 restores normal
+ * operation. */
 void tsqs_debug_withhold_publish(int on);
 
 /* ---------------------------------------------------------------------------------

@@ -23,7 +23,7 @@ ELEM_SIZE = {1: 4, 2: 4, 3: 4, 4: 8, 5: 8, 6: 8, 7: 16}
 class Plan(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int32), ("small_threshold", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("sample_count", ctypes.c_int32),
-                ("offset_mode", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("offset_mode", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
     def as_dict(self):

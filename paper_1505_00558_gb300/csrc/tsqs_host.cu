@@ -58,10 +58,27 @@ size_t kind_size(int kind) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+uint32_t g_debug_spin = 0;        // 0 = default
+uint32_t g_debug_deep = 0;        // depth-guard level; 0 = default (2 log2 n + 8)
+uint32_t g_debug_defer = 0;       // leaf-queue pause threshold; 0 = default (one level's worth)
+int g_debug_withhold = 0;         // 1: a look-back word withheld; 2: a task segment's rows
+
+// Inputs of at most this many elements run the task-parallel schedule (k_task): every
+// segment is partitioned as soon as its parent is done, with no level barrier.
+constexpr size_t kTaskMaxN = size_t(1) << 24;
+
+// Whether a sort of n elements under plan p runs the task-parallel schedule: schedule 0
+// below the size bound, 2 at any size, never with look-back offsets (their deterministic
+// layout is a level-by-level one) or schedule 1.
+bool task_schedule(const tsqs_plan &p, size_t n) {
+    if (p.offset_mode == 1 || g_debug_withhold == 1 || p.schedule == 1) return false;
+    return p.schedule == 2 || n <= kTaskMaxN;
+}
+
 struct Layout {
     size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, presort_off,
-        deep_off, dtiles_off, dchunks_off, misc_off, total;
-    uint32_t cap_front, cap_tiles, cap_leaves, leaf_defer;
+        deep_off, dtiles_off, dchunks_off, misc_off, ttask_off, trow_off, total;
+    uint32_t cap_front, cap_tiles, cap_leaves, leaf_defer, cap_tseg, cap_trow;
 };
 
 // Scratch needed for nmemb elements in nseg segments (bounds, not estimates):
@@ -72,26 +89,50 @@ struct Layout {
 //             fill items per segment, plus the small root segments: cl.  Items queue up
 //             across levels; a level's leaf pass runs once more than cl are queued, so
 //             the queue never holds more than 2 cl
+//   task schedule (task_tile > 0): segments above small_T of one depth are disjoint, and
+//             depths stop at the depth guard's level D, so <= D (n/(T+1) + 1) task
+//             segments and <= D (n/TILE + 2 (n/(T+1) + 1)) tile ids (+ the end-of-work
+//             rows); all leaves of the sort queue up for one pass: <= 3 per task segment
+//             (two children and a fill item beyond whole chunks), n/kFillChunk whole
+//             fill chunks and the small roots
 // Effective on-chip threshold: the plan's, capped by what the kind's leaf kernel holds.
 size_t eff_threshold(const tsqs_plan &plan, int leaf_max) {
     return std::min<size_t>((size_t)plan.small_threshold, (size_t)leaf_max);
 }
 
-Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int tile, int leaf_max) {
+// Depth-guard level of a sort of n elements: 2 ceil(log2(n + 1)) + 8.
+uint32_t deep_level_for(size_t n) {
+    unsigned lg = 1;
+    while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
+    return 2u * lg + 8u;
+}
+
+Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int tile, int leaf_max,
+                   int task_tile = 0) {
     Layout L{};
     const size_t T = eff_threshold(plan, leaf_max);
     const size_t cf = n / (T + 1) + nseg + 4;
     const size_t ct = n / (size_t)tile + 2 * cf + 4;
     const size_t cl = 3 * cf + n / kFillChunk + nseg + 4;
+    size_t cts = 0, ctr = 0, clt = 0;
+    if (task_tile > 0) {
+        const size_t D = std::max<size_t>(deep_level_for(n), g_debug_deep);
+        const size_t per = n / (T + 1) + 1;
+        cts = D * per + 4;
+        ctr = D * (n / (size_t)task_tile + 2 * per) + kTaskGridMax + 4;
+        clt = 3 * cts + n / kFillChunk + nseg + 4;
+    }
     L.cap_front = (uint32_t)std::min<size_t>(cf, 0xFFFFFFF0u);
     L.cap_tiles = (uint32_t)std::min<size_t>(ct, 0xFFFFFFF0u);
-    L.cap_leaves = (uint32_t)std::min<size_t>(2 * cl, 0xFFFFFFF0u);
+    L.cap_leaves = (uint32_t)std::min<size_t>(std::max(2 * cl, clt), 0xFFFFFFF0u);
     L.leaf_defer = (uint32_t)std::min<size_t>(cl, 0x7FFFFFF0u);
+    L.cap_tseg = (uint32_t)std::min<size_t>(cts, 0xFFFFFFF0u);
+    L.cap_trow = (uint32_t)std::min<size_t>(ctr, 0xFFFFFFF0u);
     size_t off = 0;
     L.alt_off = off;            off = align_up(off + n * es + 16, 256);
     L.front_off[0] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
     L.front_off[1] = off;       off = align_up(off + cf * sizeof(SegDesc), 256);
-    L.leaves_off = off;         off = align_up(off + 2 * cl * sizeof(LeafItem), 256);
+    L.leaves_off = off;         off = align_up(off + std::max(2 * cl, clt) * sizeof(LeafItem), 256);
     L.tseg_off = off;           off = align_up(off + ct * sizeof(uint32_t), 256);
     L.tstat_off = off;          off = align_up(off + ct * sizeof(unsigned long long), 256);
     L.done_off = off;           off = align_up(off + cf * sizeof(uint32_t), 256);
@@ -101,6 +142,8 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     L.dtiles_off = off;         off = align_up(off + (cf + 1) * sizeof(uint32_t), 256);
     L.dchunks_off = off;        off = align_up(off + (cf + 1) * sizeof(uint32_t), 256);
     L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
+    L.ttask_off = off;          off = align_up(off + cts * sizeof(TaskSeg), 256);
+    L.trow_off = off;           off = align_up(off + ctr * sizeof(uint32_t), 256);
     L.total = off;
     return L;
 }
@@ -112,7 +155,7 @@ void fill_default_plan(int key_kind, size_t, tsqs_plan *p) {
     p->ctas_per_sm = 0;           // occupancy-derived
     p->sample_count = 31;
     p->offset_mode = 0;
-    p->pad = 0;
+    p->schedule = 0;
     p->seed = 0x5EED5EED12345678ull;
 }
 
@@ -128,13 +171,9 @@ void normalise_plan(tsqs_plan *p) {
     if (p->seed == 0) p->seed = d.seed;
     if (p->ctas_per_sm < 0) p->ctas_per_sm = 0;
     if (p->offset_mode != 1) p->offset_mode = 0;
+    if (p->schedule < 0 || p->schedule > 2) p->schedule = 0;
     if (p->tile_items < 0 || p->tile_items >= kPartVariants) p->tile_items = 0;
 }
-
-uint32_t g_debug_spin = 0;        // 0 = default
-uint32_t g_debug_deep = 0;        // depth-guard level; 0 = default (2 log2 n + 8)
-uint32_t g_debug_defer = 0;       // leaf-queue pause threshold; 0 = default (one level's worth)
-int g_debug_withhold = 0;
 
 }  // namespace
 
@@ -148,7 +187,9 @@ struct tsqs_ctx {
     size_t scratch_bytes = 0;
     cudaGraph_t graph[8] = {};
     cudaGraphExec_t exec[8] = {};
-    int part_grid[8] = {}, leaf_grid[8] = {};
+    cudaGraph_t graph_task[8] = {};      // the task-parallel schedule's graph per kind
+    cudaGraphExec_t exec_task[8] = {};
+    int part_grid[8] = {}, leaf_grid[8] = {}, task_grid[8] = {};
     bool attrs_set[8] = {};
     cudaEvent_t done_ev = nullptr;
     bool ev_valid = false;
@@ -210,9 +251,14 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     int occ_p = 0, occ_l = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pv.k_partition, pv.threads, pv.smem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem));
+    int occ_t = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, o->k_task, o->task_block, 0));
     if (c->plan.ctas_per_sm > 0) occ_p = std::min(occ_p, c->plan.ctas_per_sm);
     c->part_grid[k] = std::max(1, occ_p) * c->sms;
     c->leaf_grid[k] = std::max(1, occ_l) * c->sms;
+    // every block of the task kernel resident at once (the end-of-work rows cover one
+    // claim per block)
+    c->task_grid[k] = std::min<int>(std::max(1, occ_t) * c->sms, (int)kTaskGridMax);
     c->attrs_set[k] = true;
     return TSQS_OK;
 }
@@ -223,8 +269,16 @@ int ctx_quiesce(tsqs_ctx *c) {
     return TSQS_OK;
 }
 
-int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile, int leaf_max) {
-    const Layout L = make_layout(n, nseg, es, c->plan, tile, leaf_max);
+// Tile size of the task kernel when a sort of n elements under plan p runs the task
+// schedule, else 0 (no task tables in the layout).
+int task_tile_for(const KindOps *o, const tsqs_plan &p, size_t n) {
+    return task_schedule(p, n) ? o->task_tile : 0;
+}
+
+int ctx_ensure_scratch(tsqs_ctx *c, const KindOps *o, size_t n, size_t nseg) {
+    const size_t es = (size_t)o->elem_size;
+    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile, o->leaf_max,
+                                 task_tile_for(o, c->plan, n));
     if (c->scratch && L.total <= c->scratch_bytes) return TSQS_OK;
     int rc = ctx_quiesce(c);
     if (rc) return rc;
@@ -246,10 +300,13 @@ int ctx_ensure_scratch(tsqs_ctx *c, size_t n, size_t nseg, size_t es, int tile, 
 
 // Fills the per-call description.  The scratch buffer gets the same 16-byte phase as
 // base so that both buffers use the same tile geometry.
+// task: the call runs the task schedule (its tables are filled in, and `tile` is the
+// task kernel's).
 int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t *offs,
-             size_t nseg, Job *j) {
+             size_t nseg, Job *j, bool task = false) {
     const size_t es = (size_t)o->elem_size;
-    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile, o->leaf_max);
+    const int task_tile = task ? o->task_tile : 0;
+    const Layout L = make_layout(n, nseg, es, c->plan, part_of(o, c->plan).tile, o->leaf_max, task_tile);
     if (L.total > c->scratch_bytes) return TSQS_EINTERNAL;
     memset(j, 0, sizeof(*j));
     const uintptr_t b = (uintptr_t)base;
@@ -279,17 +336,28 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     j->samples = (uint32_t)c->plan.sample_count;
     j->vec_off = (uint32_t)((b / es) % (16 / es));
     j->spin_limit = g_debug_spin ? g_debug_spin : kDefaultSpin;
-    j->pad = g_debug_withhold ? 2u : 0u;
+    j->pad = g_debug_withhold == 1 ? 2u : g_debug_withhold == 2 ? 4u : 0u;
     // depth cap: far above what sampled medians need (about log2(n / T) + a few)
     unsigned lg = 1;
     while ((1ull << lg) < (unsigned long long)n + 1 && lg < 63) lg++;
     j->max_levels = 256u + 8u * lg;
     j->deep_level = g_debug_deep ? g_debug_deep : 2u * lg + 8u;
-    j->offset_mode = (c->plan.offset_mode == 1 || g_debug_withhold) ? 1u : 0u;
+    j->offset_mode = (c->plan.offset_mode == 1 || g_debug_withhold == 1) ? 1u : 0u;
     j->tile = (uint32_t)part_of(o, c->plan).tile;
     j->seed = c->plan.seed;
+    if (task_tile) {
+        j->tile = (uint32_t)task_tile;
+        j->tseg = (TaskSeg *)(c->scratch + L.ttask_off);
+        j->trow = (uint32_t *)(c->scratch + L.trow_off);
+        j->cap_tseg = L.cap_tseg;
+        j->cap_trow = L.cap_trow;
+        j->task_grid = (uint32_t)c->task_grid[o->kind];
+    }
     return TSQS_OK;
 }
+
+int add_deep_branch(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, cudaGraphNode_t after,
+                    cudaGraphConditionalHandle h_if);
 
 // Adds the nodes of one whole sort of kind o to graph g, the first of them depending on
 // `dep` (nullptr: none).  Every kernel reads the per-call Job from c->d_job.
@@ -386,15 +454,24 @@ int build_sort_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     kp.blockDim = dim3(32);
     kp.kernelParams = argso;
     CK(cudaGraphAddKernelNode(&n_octl, outer, &n_last, 1, &kp));
-    // depth guard (IF some segment reached the bound): prep, tile sorts, a WHILE over
-    // the stages, finish
+    return add_deep_branch(c, o, g, n_outer, h_if);
+}
+
+// Adds the depth guard's branch to graph g after node `after`: IF (h_if) some segment
+// reached the bound, prep, tile sorts, a WHILE over the stages, finish.
+int add_deep_branch(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, cudaGraphNode_t after,
+                    cudaGraphConditionalHandle h_if) {
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    cudaKernelNodeParams kp{};
     cudaGraphNodeParams ip{};
     ip.type = cudaGraphNodeTypeConditional;
     ip.conditional.handle = h_if;
     ip.conditional.type = cudaGraphCondTypeIf;
     ip.conditional.size = 1;
     cudaGraphNode_t n_if;
-    CK(cudaGraphAddNode(&n_if, g, &n_outer, nullptr, 1, &ip));
+    CK(cudaGraphAddNode(&n_if, g, &after, nullptr, 1, &ip));
     cudaGraph_t dg = ip.conditional.phGraph_out[0];
     cudaGraphConditionalHandle hd;
     CK(cudaGraphConditionalHandleCreate(&hd, dg, 0, cudaGraphCondAssignDefault));
@@ -454,6 +531,68 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
     return TSQS_OK;
 }
 
+// The task schedule's graph for kind o:
+//     orient -> check -> presort -> task init -> task kernel -> leaf pass
+//       -> IF (some segment reached the depth guard) { deep branch }
+// The task kernel's last block sets the IF condition.
+int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g) {
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    cudaKernelNodeParams kp{};
+    cudaGraphNode_t n_ori, n_chk, n_pre, n_init, n_task, n_leaf;
+    kp.func = (void *)o->k_orient;
+    kp.gridDim = dim3(c->sms * 4);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_ori, g, nullptr, 0, &kp));
+    kp.func = (void *)o->k_check;
+    CK(cudaGraphAddKernelNode(&n_chk, g, &n_ori, 1, &kp));
+    kp.func = (void *)o->k_presort;
+    CK(cudaGraphAddKernelNode(&n_pre, g, &n_chk, 1, &kp));
+    kp.func = (void *)o->k_task_init;
+    kp.gridDim = dim3(c->sms * 2);
+    CK(cudaGraphAddKernelNode(&n_init, g, &n_pre, 1, &kp));
+    cudaGraphConditionalHandle h_if;
+    CK(cudaGraphConditionalHandleCreate(&h_if, g, 0, cudaGraphCondAssignDefault));
+    int use_h = 1;
+    void *argst[] = {&pj, &pc, &h_if, &use_h};
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_task;
+    kp.gridDim = dim3(c->task_grid[o->kind]);
+    kp.blockDim = dim3(o->task_block);
+    kp.kernelParams = argst;
+    CK(cudaGraphAddKernelNode(&n_task, g, &n_init, 1, &kp));
+    int leaf_last = 1;
+    void *argsl[] = {&pj, &pc, &leaf_last};
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_leaf;
+    kp.gridDim = dim3(c->leaf_grid[o->kind]);
+    kp.blockDim = dim3(o->leaf_block);
+    kp.sharedMemBytes = (unsigned)o->leaf_smem;
+    kp.kernelParams = argsl;
+    CK(cudaGraphAddKernelNode(&n_leaf, g, &n_task, 1, &kp));
+    return add_deep_branch(c, o, g, n_leaf, h_if);
+}
+
+int ctx_build_task_graph(tsqs_ctx *c, const KindOps *o) {
+    const int k = o->kind;
+    if (c->exec_task[k]) return TSQS_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    int rc = build_task_nodes(c, o, g);
+    cudaGraphExec_t ex = nullptr;
+    if (rc == TSQS_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) rc = TSQS_ECUDA;
+    if (rc) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return rc;
+    }
+    c->graph_task[k] = g;
+    c->exec_task[k] = ex;
+    return TSQS_OK;
+}
+
 // Depth guard, host-driven (the graph runs the same kernels under a WHILE node).
 cudaError_t run_deep_host(tsqs_ctx *c, const KindOps *o, cudaStream_t s, Job *pj, Ctl *pc) {
     cudaGraphConditionalHandle hd = 0;
@@ -494,15 +633,16 @@ int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t n
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, n, offs ? nseg : 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
-    if ((rc = ctx_build_graph(c, o))) return rc;
+    if ((rc = ctx_ensure_scratch(c, o, n, offs ? nseg : 1))) return rc;
+    const bool task = task_schedule(c->plan, n);
+    if ((rc = task ? ctx_build_task_graph(c, o) : ctx_build_graph(c, o))) return rc;
     Job j;
-    if ((rc = make_job(c, o, base, n, offs, nseg, &j))) return rc;
+    if ((rc = make_job(c, o, base, n, offs, nseg, &j, task))) return rc;
     if (out) j.out = out;
     if (c->ev_valid) CK(cudaStreamWaitEvent(stream, c->done_ev, 0));
     k_setup<<<1, 256, 0, stream>>>(c->d_job, c->d_ctl, j);
     CK(cudaGetLastError());
-    CK(cudaGraphLaunch(c->exec[key_kind], stream));
+    CK(cudaGraphLaunch(task ? c->exec_task[key_kind] : c->exec[key_kind], stream));
     CK(cudaEventRecord(c->done_ev, stream));
     c->ev_valid = true;
     return TSQS_OK;
@@ -596,6 +736,8 @@ void tsqs_ctx_destroy(tsqs_ctx *c) {
         for (int k = 0; k < 8; k++) {
             if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
             if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+            if (c->exec_task[k]) cudaGraphExecDestroy(c->exec_task[k]);
+            if (c->graph_task[k]) cudaGraphDestroy(c->graph_task[k]);
         }
         for (auto &h : c->held) {
             cudaGraphExecDestroy(h.exec);
@@ -633,8 +775,12 @@ int tsqs_ctx_set_plan(tsqs_ctx *c, const tsqs_plan *plan) {
     for (int k = 0; k < 8; k++) {            // grids depend on the plan
         if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
         if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+        if (c->exec_task[k]) cudaGraphExecDestroy(c->exec_task[k]);
+        if (c->graph_task[k]) cudaGraphDestroy(c->graph_task[k]);
         c->exec[k] = nullptr;
         c->graph[k] = nullptr;
+        c->exec_task[k] = nullptr;
+        c->graph_task[k] = nullptr;
         c->attrs_set[k] = false;
     }
     return TSQS_OK;
@@ -681,8 +827,7 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     }
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb_total, offs ? nseg : 1, elem_size,
-                                 part_of(o, c->plan).tile, o->leaf_max))) return rc;
+    if ((rc = ctx_ensure_scratch(c, o, nmemb_total, offs ? nseg : 1))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, nmemb_total, offs, offs ? nseg : 1, &j))) return rc;
     Job *pj = c->d_job;
@@ -739,8 +884,7 @@ int tsqs_ctx_reserve(tsqs_ctx *c, size_t nmemb_total, size_t nseg, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     int rc = ctx_init_device(c);
     if (rc) return rc;
-    return ctx_ensure_scratch(c, nmemb_total, nseg ? nseg : 1, elem_size, part_of(o, c->plan).tile,
-                              o->leaf_max);
+    return ctx_ensure_scratch(c, o, nmemb_total, nseg ? nseg : 1);
 }
 
 size_t tsqs_ctx_scratch_bytes(const tsqs_ctx *c) { return c ? c->scratch_bytes : 0; }
@@ -753,7 +897,8 @@ size_t tsqs_scratch_bytes_for(size_t nmemb_total, size_t nseg, size_t elem_size,
     tsqs_plan p;
     if (plan) p = *plan; else fill_default_plan(kind, nmemb_total, &p);
     normalise_plan(&p);
-    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, part_of(o, p).tile, o->leaf_max).total;
+    return make_layout(nmemb_total, nseg ? nseg : 1, elem_size, p, part_of(o, p).tile, o->leaf_max,
+                       task_tile_for(o, p, nmemb_total)).total;
 }
 
 int tsqs_ctx_device_status(tsqs_ctx *c, void *stream) {
@@ -778,7 +923,8 @@ int tsqs_ctx_stats(tsqs_ctx *c, void *stream, tsqs_stats *out) {
     out->leaf_items = h.leaf_items;
     out->presorted_keys = h.presorted;
     out->deep_sorted_keys = h.deep_keys;
-    const uint32_t nl = std::min<uint32_t>(h.level, (uint32_t)kStatLevels);
+    // levels run (level-by-level schedule) or depths reached (task schedule)
+    const uint32_t nl = std::min<uint32_t>(std::max(h.level, h.levels_done), (uint32_t)kStatLevels);
     out->level_keys_count = nl;
     for (uint32_t i = 0; i < nl; i++) out->level_keys[i] = h.level_keys[i];
     return TSQS_OK;
@@ -871,7 +1017,7 @@ int tsqs_sort_wide(void *base, size_t nmemb, size_t elem_size, size_t key_offset
 void tsqs_debug_set_spin_limit(uint32_t polls) { g_debug_spin = polls; }
 void tsqs_debug_set_deep_level(uint32_t level) { g_debug_deep = level; }
 void tsqs_debug_set_leaf_defer(uint32_t items) { g_debug_defer = items; }
-void tsqs_debug_withhold_publish(int on) { g_debug_withhold = on ? 1 : 0; }
+void tsqs_debug_withhold_publish(int on) { g_debug_withhold = on == 2 ? 2 : on ? 1 : 0; }
 
 // ---------------------------------------------------------------------------------
 // host-memory sort: device staging buffer owned by the default context's side store
@@ -952,7 +1098,7 @@ int tsqs_ctx_sort_host_stream(tsqs_ctx *c, const void *const *h_in, void *const 
     const size_t slot_bytes = std::max<size_t>(max_n * es, 16);
     if ((rc = ctx_stream_setup(c, slot_bytes, count))) return rc;
     if (max_n > 1) {
-        if ((rc = ctx_ensure_scratch(c, max_n, 1, es, part_of(o, c->plan).tile, o->leaf_max))) return rc;
+        if ((rc = ctx_ensure_scratch(c, o, max_n, 1))) return rc;
         if ((rc = ctx_build_graph(c, o))) return rc;
     }
     int first = TSQS_OK;
@@ -1013,7 +1159,7 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
+    if ((rc = ctx_ensure_scratch(c, o, nmemb, 1))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, nmemb, nullptr, 0, &j))) return rc;
     if (c->ev_valid) CK(cudaStreamWaitEvent(s, c->done_ev, 0));
@@ -1028,12 +1174,44 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     int leaf_final = 0, leaf_last = 1;
     void *argsl[] = {&pj, &pc, &leaf_final};
     void *argsl_last[] = {&pj, &pc, &leaf_last};
+    const bool task = task_schedule(c->plan, nmemb);
+    if (task) {
+        if ((rc = make_job(c, o, base, nmemb, nullptr, 0, &j, true))) return rc;
+    }
     cudaEvent_t ev[4];
     for (auto &e : ev) CK(cudaEventCreate(&e));
     k_setup<<<1, 256, 0, s>>>(c->d_job, c->d_ctl, j);
     CK(cudaLaunchKernel(o->k_orient, dim3(c->sms * 4), dim3(256), args2, 0, s));
     CK(cudaLaunchKernel(o->k_check, dim3(c->sms * 4), dim3(256), args2, 0, s));
     CK(cudaLaunchKernel(o->k_presort, dim3(c->sms * 4), dim3(256), args2, 0, s));
+    if (task) {
+        // task schedule: init, the task kernel, the leaf pass, the depth guard if needed
+        void *argst[] = {&pj, &pc, &h, &use_h};
+        CK(cudaLaunchKernel(o->k_task_init, dim3(c->sms * 2), dim3(256), args2, 0, s));
+        CK(cudaEventRecord(ev[0], s));
+        CK(cudaLaunchKernel(o->k_task, dim3(c->task_grid[k]), dim3(o->task_block), argst, 0, s));
+        CK(cudaEventRecord(ev[1], s));
+        CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl_last,
+                            (size_t)o->leaf_smem, s));
+        CK(cudaEventRecord(ev[2], s));
+        Ctl hc;
+        CK(cudaMemcpyAsync(&hc, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float ms = 0.f, lms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&lms, ev[1], ev[2]));
+        if (hc.status == 0u && hc.ndeep != 0u) CK(run_deep_host(c, o, s, c->d_job, c->d_ctl));
+        for (auto &e : ev) cudaEventDestroy(e);
+        if (max_levels >= 1) {
+            if (h_ms) h_ms[0] = ms;
+            if (h_leaf_ms) h_leaf_ms[0] = lms;
+            if (h_keys) h_keys[0] = hc.partition_keys;
+        }
+        if (levels) *levels = 1;
+        CK(cudaEventRecord(c->done_ev, s));
+        c->ev_valid = true;
+        return TSQS_OK;
+    }
     CK(cudaLaunchKernel(o->k_init, dim3(c->sms * 2), dim3(256), args2, 0, s));
     int L = 0;
     for (;;) {
@@ -1101,7 +1279,7 @@ int tsqs_debug_pivot(const void *base, size_t nmemb, size_t elem_size, int key_k
     const KindOps *o = get_ops(key_kind);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, 1, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
+    if ((rc = ctx_ensure_scratch(c, o, nmemb, 1))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)base, nmemb, nullptr, 0, &j))) return rc;
     const Layout L = make_layout(nmemb, 1, elem_size, c->plan, part_of(o, c->plan).tile, o->leaf_max);
@@ -1150,7 +1328,7 @@ int tsqs_debug_partition(const void *src, void *dst, size_t nmemb, size_t elem_s
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
-    if ((rc = ctx_ensure_scratch(c, nmemb, nseg, elem_size, part_of(o, c->plan).tile, o->leaf_max))) return rc;
+    if ((rc = ctx_ensure_scratch(c, o, nmemb, nseg))) return rc;
     Job j;
     if ((rc = make_job(c, o, (void *)src, nmemb, d_seg_offsets, nseg, &j))) return rc;
     j.alt = dst;

@@ -22,6 +22,9 @@ constexpr uint32_t kFillChunk = 16384;      // =p fills are split into items of 
 constexpr uint32_t kInlineFill = 16;        // =p runs up to this long are written by the level-end kernel
 constexpr int kMaxSmall = 4096;             // largest on-chip segment
 constexpr int kStatLevels = 64;
+constexpr uint32_t kTaskEnd = 0xFFFFFFFFu;  // tile-row value: no more work
+constexpr uint32_t kTaskGridMax = 4096;     // end-of-work rows reserved past the last tile
+
 
 enum LeafKind : uint32_t { LEAF_SORT = 0, LEAF_FILL = 1 };
 // LeafItem::kind flag: the item's keys are in buffer 1 (alt) rather than buffer 0
@@ -35,6 +38,20 @@ struct SegDesc {
     uint32_t ntiles;
     uint64_t piv_lo, piv_hi;  // canonical pivot (hi used by 16-byte records only)
 };
+
+// A segment of the task-parallel schedule (inputs up to a size bound, see k_task):
+// partitioned as soon as it is pushed, with its own finished-tile count and cursor.
+struct alignas(16) TaskSeg {
+    uint64_t begin, end;
+    int64_t  s0;              // element index where tile 0 starts (16-byte aligned, <= begin)
+    uint64_t piv_lo, piv_hi;  // canonical pivot
+    uint32_t tile_begin;      // first global tile id (tile ids run over the whole sort)
+    uint32_t ntiles;
+    uint32_t depth;           // recursion depth: keys in buffer depth % 2
+    uint32_t done;            // tiles finished
+    unsigned long long cursor;   // reserved (#<p | #>p << 32)
+};
+static_assert(sizeof(TaskSeg) == 64, "TaskSeg is four 16-byte words");
 
 struct LeafItem {
     uint64_t begin;
@@ -66,6 +83,10 @@ struct Ctl {
     uint32_t blocks_done;     // level-end blocks finished (last one runs level control)
     uint32_t more;            // levels remain (after a leaf pass if cont is 0); host-driven
                               // mode reads it
+    uint32_t tclaim;          // task schedule: tile ids claimed
+    uint32_t talloc;          // task schedule: tile ids given to pushed segments
+    uint32_t tsegs;           // task schedule: segments pushed
+    uint32_t live;            // task schedule: pushed segments not yet finished
     uint64_t front_keys[2];
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;
@@ -108,8 +129,16 @@ struct Job {
     uint32_t max_levels;      // level cap; exceeding it stops the loop with an error
     uint32_t offset_mode;     // 0: per-segment atomic cursor, 1: decoupled look-back
     uint32_t tile;            // keys per partition tile of the partition kernel in use
+                              // (of the task kernel in the task schedule)
     uint32_t pad3;
     uint64_t seed;            // sample jitter seed
+    // task schedule (k_task); null / zero when the call runs level by level
+    TaskSeg *tseg;            // pushed segments
+    uint32_t *trow;           // tile id -> segment + 1 (0: not pushed yet; kTaskEnd: no more
+                              // work), zeroed by k_orient at the start of every call
+    uint32_t cap_tseg, cap_trow;
+    uint32_t task_grid;       // blocks of k_task (end-of-work rows to write)
+    uint32_t pad4;
     // step-level test hooks
     const void *dbg_pivots;   // debug partition: pivots of the given segments
     uint64_t *dbg_counts;     // debug partition: (#<p, #>p) per segment
@@ -140,6 +169,8 @@ struct KindOps {
     const void *k_deep_prep, *k_deep_tiles, *k_deep_stage, *k_deep_finish;
     int deep_smem;            // dynamic shared memory of the on-chip deep stages
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
+    const void *k_task_init, *k_task;   // task schedule
+    int task_block, task_tile;
 };
 
 // Large elements (tsqs_wide.cu): (key, index) records of every element, and the gather

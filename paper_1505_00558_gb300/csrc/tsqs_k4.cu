@@ -1,10 +1,12 @@
 // tsqs_k4.cu -- kernel instantiations for 4-byte keys.
 #include "tsqs_kernels.cuh"
+#include "tsqs_task.cuh"
 
 namespace tsqs {
 
 namespace {
 constexpr int kLeafBlock = 128, kLeafMaxE = 32, kPivotBlock = 256;
+constexpr int kTaskBlock = 256, kTaskItems = 16;   // task schedule: 16 KB tiles
 
 template <int KIND, int BLOCK, int ITEMS, int NBUF>
 PartVariant part_variant() {
@@ -45,6 +47,10 @@ KindOps make_ops() {
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;
     o.k_dbg_counts = (const void *)k_dbg_counts;
     o.k_dbg_pivot = (const void *)k_dbg_pivot<KIND>;
+    o.k_task_init = (const void *)k_task_init<KIND>;
+    o.k_task = (const void *)k_task<KIND, kTaskBlock, kTaskItems>;
+    o.task_block = kTaskBlock;
+    o.task_tile = kTaskBlock * kTaskItems;
     return o;
 }
 }  // namespace

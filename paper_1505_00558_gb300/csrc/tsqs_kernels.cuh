@@ -371,6 +371,11 @@ __global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const typename K::S *src = buffer<K>(job, 0);
+    if (job->trow) {                   // task schedule: this call's tile rows start empty
+        const uint32_t stride = gridDim.x * blockDim.x;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < job->cap_trow; i += stride)
+            job->trow[i] = 0u;
+    }
     for (uint64_t s = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
         uint64_t b, e;
         root_bounds(job, s, b, e);
@@ -485,7 +490,20 @@ __global__ void k_presort(const Job *__restrict__ job, Ctl *ctl) {
 // fifteenther, with every position shifted by a seeded random amount (Section V.C).
 // ---------------------------------------------------------------------------------
 
-template <class K>
+// L2 loads (no L1 allocation) of one storage element: for data other blocks of the same
+// launch have written since this block last read that memory.
+__device__ __forceinline__ unsigned int ldcg_key(const unsigned int *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ldcg_key(const unsigned long long *p) { return __ldcg(p); }
+__device__ __forceinline__ Rec16 ldcg_key(const Rec16 *p) {
+    const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+    Rec16 r;
+    r.key = q.x;
+    r.pay = q.y;
+    return r;
+}
+
+// kL2: read the samples from L2 (the task schedule samples keys written in the same launch)
+template <class K, bool kL2 = false>
 __device__ typename K::C sample_pivot(const typename K::S *src, uint64_t b, uint64_t e,
                                       uint32_t S_req, uint64_t seed, uint64_t *positions) {
     using C = typename K::C;
@@ -521,7 +539,7 @@ __device__ typename K::C sample_pivot(const typename K::S *src, uint64_t b, uint
             // down (Lemire's multiply-shift range reduction), else z mod w
             const uint64_t pos = lo + (narrow ? (((z >> 32) * w) >> 32) : z % w);
             if (positions) positions[k] = pos;
-            v[h] = K::canon(src[pos]);
+            v[h] = K::canon(kL2 ? ldcg_key(src + pos) : src[pos]);
         }
     }
     // the median is the sample of rank (S - 1) / 2: sort the samples across the warp

@@ -1,0 +1,442 @@
+// tsqs_task.cuh -- the task-parallel schedule of the three-way partition sort (sm_103a).
+//
+// Below a size bound the level-synchronous loop is latency-bound: every level waits for
+// its slowest segment and pays three dependent launches (pivot, partition, level end)
+// whose work is a handful of tiles.  Here the recursion of Section III.F runs without
+// level barriers, in one persistent launch:
+//   - tile ids run over the whole sort and are claimed in one global order; a segment
+//     gets a range of ids when it is pushed, and each id's row (segment index + 1; the
+//     rows are zeroed by the first kernel of the call) is written once the segment's
+//     descriptor and sampled median (Section III.H, V.C) are in memory;
+//   - a block that claimed an id whose row is not written yet polls it (bounded);
+//   - a tile is classified against p once, its <p and >p elements are packed at the two
+//     ends of the segment through one 64-bit atomic on the segment's cursor (the roles of
+//     the paper's l and r), and the =p elements are never written or compared again;
+//   - the block that finishes a segment's last tile reads the final (#<p, #>p), writes
+//     the =p run (or queues fill items for a long one) and pushes both children: to the
+//     leaf queue (<= small_T, Section IV's role), to the depth guard's queue, or as new
+//     segments partitioned as soon as their blocks pick them up;
+//   - a count of live segments falling to zero ends the launch: the block that sees it
+//     writes end-of-work rows for every block still polling.
+// Keys of depth d are in buffer d % 2, as level d's are in the level-synchronous loop,
+// and the output of every step (leaf items, fills, deep items) is the same.
+#pragma once
+#include "tsqs_kernels.cuh"
+
+namespace tsqs {
+
+constexpr uint32_t kTaskInlineFill = 1u << 16;   // =p runs up to this long are written by the
+                                                 // block that finishes their segment
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Descriptor of segment si from L2 (it may have been written in this launch after this
+// block cached a neighbouring one).
+__device__ __forceinline__ TaskSeg load_task_seg(const TaskSeg *p) {
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+    const ulonglong2 w0 = __ldcg(q), w1 = __ldcg(q + 1), w2 = __ldcg(q + 2), w3 = __ldcg(q + 3);
+    TaskSeg t;
+    t.begin = w0.x;
+    t.end = w0.y;
+    t.s0 = (int64_t)w1.x;
+    t.piv_lo = w1.y;
+    t.piv_hi = w2.x;
+    t.tile_begin = (uint32_t)w2.y;
+    t.ntiles = (uint32_t)(w2.y >> 32);
+    t.depth = (uint32_t)w3.x;
+    t.done = (uint32_t)(w3.x >> 32);
+    t.cursor = w3.y;
+    return t;
+}
+
+// 16-byte L2 load of V storage elements (address 16-byte aligned).
+template <class S, int V>
+__device__ __forceinline__ void ldcg_vec(const S *p, S *out) {
+    union { uint4 q; S s[V]; } u;
+    u.q = __ldcg(reinterpret_cast<const uint4 *>(p));
+#pragma unroll
+    for (int j = 0; j < V; j++) out[j] = u.s[j];
+}
+
+// Threads t (of nt) write val to out[b, e): scalar up to the first 16-byte boundary,
+// 16-byte stores for the body, scalar tail.
+template <class S, int V>
+__device__ __forceinline__ void fill_span(S *out, uint64_t b, uint64_t e, S val, uint32_t vec_off,
+                                          uint32_t t, uint32_t nt) {
+    if (e <= b) return;
+    const uint64_t cnt = e - b;
+    uint64_t head = (V - ((b + vec_off) % V)) % V;
+    if (head > cnt) head = cnt;
+    const uint64_t nvec = (cnt - head) / V;
+    if (t < head) out[b + t] = val;
+    S w[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) w[j] = val;
+    for (uint64_t q = t; q < nvec; q += nt) stg_vec<S, V>(out + b + head + q * V, w);
+    const uint64_t body_end = head + nvec * V;
+    if (t < cnt - body_end) out[b + body_end + t] = val;
+}
+
+// One warp: pushes [b, e) (keys in buffer d % 2) as a task segment of depth d: samples
+// its median, takes a descriptor and a range of tile ids, writes the descriptor, then
+// the tile rows.  Returns false (status set) when a table is full.  `withhold`: the
+// rows of segment 0 are not written (test of the bounded wait).
+template <class K>
+__device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint32_t d,
+                          bool withhold) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const typename K::C p = sample_pivot<K, true>(buffer<K>(job, (int)(d & 1u)), b, e,
+                                                  job->samples, job->seed, nullptr);
+    const int64_t s0 = tile_origin<K::V>(b, job->vec_off);
+    const uint32_t nt = tiles_for(e, s0, (int)job->tile);
+    uint32_t fi = 0, tb = 0, ok = 0;
+    if (lane == 0) {
+        fi = atomicAdd(&ctl->tsegs, 1u);
+        tb = atomicAdd(&ctl->talloc, nt);
+        ok = (fi < job->cap_tseg && (uint64_t)tb + nt + kTaskGridMax <= job->cap_trow) ? 1u : 0u;
+        if (ok) {
+            TaskSeg ts;
+            ts.begin = b;
+            ts.end = e;
+            ts.s0 = s0;
+            c_words(p, ts.piv_lo, ts.piv_hi);
+            ts.tile_begin = tb;
+            ts.ntiles = nt;
+            ts.depth = d;
+            ts.done = 0u;
+            ts.cursor = 0ull;
+            job->tseg[fi] = ts;
+            const unsigned long long m = e - b;
+            if (d < (uint32_t)kStatLevels) atomicAdd((unsigned long long *)&ctl->level_keys[d], m);
+            atomicAdd((unsigned long long *)&ctl->partition_keys, m);
+            atomicMax(&ctl->levels_done, d + 1u);
+        } else {
+            set_status(ctl, TSQS_EINTERNAL);
+        }
+    }
+    fi = __shfl_sync(0xffffffffu, fi, 0);
+    tb = __shfl_sync(0xffffffffu, tb, 0);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    // descriptor before rows: lane 0's stores, the warp barrier, then every lane's fence
+    // ahead of its row stores (a release that covers lane 0's stores)
+    __syncwarp();
+    __threadfence();
+    if (withhold && fi == 0u) return true;
+    for (uint32_t k = lane; k < nt; k += 32u) st_relaxed(job->trow + tb + k, fi + 1u);
+    return true;
+}
+
+// One thread: queues [b, e) (keys in buffer par) for the leaf pass.
+__device__ __forceinline__ void push_leaf(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, int par) {
+    const uint32_t li = atomicAdd(&ctl->nleaf, 1u);
+    if (li >= job->cap_leaves) { set_status(ctl, TSQS_EINTERNAL); return; }
+    LeafItem it;
+    it.begin = b;
+    it.len = (uint32_t)(e - b);
+    it.kind = LEAF_SORT | (par ? kLeafInAlt : 0u);
+    it.v_lo = 0;
+    it.v_hi = 0;
+    job->leaves[li] = it;
+}
+
+// Seeds the task schedule: one warp per root segment (grid-stride).  Roots above the
+// on-chip threshold become task segments of depth 0, smaller ones leaf items; the last
+// block writes end-of-work rows if no task was pushed.
+template <int KIND>
+__global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
+    using K = Key<KIND>;
+    __shared__ uint32_t s_last;
+    const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const bool withhold = (job->pad & 4u) != 0u;
+    uint32_t pushed = 0;
+    for (uint64_t s = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
+        uint64_t b, e;
+        root_bounds(job, s, b, e);
+        if (e < b || e > job->n || e - b >= (1ull << 31)) {
+            if (lane == 0) set_status(ctl, TSQS_EINVAL);
+            continue;
+        }
+        if (e - b <= 1) continue;
+        if (job->presort[s] != 0u) continue;             // already in order (presortedness pass)
+        if (e - b > job->small_T) {
+            if (push_task<K>(job, ctl, b, e, 0u, withhold)) pushed++;
+        } else if (lane == 0) {
+            push_leaf(job, ctl, b, e, 0);
+        }
+    }
+    if (lane == 0 && pushed) atomicAdd(&ctl->live, pushed);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl->blocks_done, 1u) + 1u == gridDim.x ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (*(volatile const uint32_t *)&ctl->live == 0u) {
+            const uint32_t ta = *(volatile const uint32_t *)&ctl->talloc;
+            for (uint32_t g = threadIdx.x; g < job->task_grid && (uint64_t)ta + g < job->cap_trow; g += blockDim.x)
+                st_relaxed(job->trow + ta + g, kTaskEnd);
+        }
+        if (threadIdx.x == 0) ctl->blocks_done = 0u;
+    }
+}
+
+// The task kernel (persistent; BLOCK threads, tiles of BLOCK x ITEMS keys).  When the
+// last segment finishes, the block that finished it sets the depth guard's branch
+// (graph launches: use_handle) from the deep queue.
+template <int KIND, int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl *ctl,
+                                                cudaGraphConditionalHandle h_deep, int use_handle) {
+    using K = Key<KIND>;
+    using S = typename K::S;
+    using C = typename K::C;
+    using D = typename K::D;
+    constexpr int TILE = BLOCK * ITEMS, V = K::V, NV = ITEMS / V, NW = BLOCK / 32;
+    static_assert(ITEMS % V == 0 && ITEMS <= 32 && TILE < 65536 && NW >= 4, "tile shape");
+    __shared__ __align__(16) S buf[TILE + V];      // staged runs + one dummy 16-byte slot
+    __shared__ uint32_t wsum[NW];
+    __shared__ TaskSeg s_seg;
+    __shared__ uint32_t s_si, s_tile, s_cmd, s_last, s_push[2], s_end, s_ta;
+    __shared__ unsigned long long s_resv;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = (int64_t)job->n;
+    const uint32_t vec_off = job->vec_off;
+    // element range of the buffers that 16-byte loads may touch
+    const int64_t e_lo = (int64_t)((V - (int64_t)vec_off % V) % V);
+    const int64_t e_hi = n - ((n + (int64_t)vec_off) % V);
+    const uint64_t T = job->small_T;
+    const uint32_t spin_limit = job->spin_limit;
+
+    for (;;) {
+        // ---- claim the next tile id and wait for its row
+        if (tid == 0) {
+            uint32_t cmd = 1u;
+            const uint32_t t = atomicAdd(&ctl->tclaim, 1u);
+            if (t >= job->cap_trow) {
+                set_status(ctl, TSQS_EINTERNAL);
+            } else {
+                uint32_t polls = 0;
+                for (;;) {
+                    const uint32_t r = ld_acquire(job->trow + t);
+                    if (r != 0u) {
+                        if (r != kTaskEnd) {
+                            const uint32_t si = r - 1u;
+                            s_si = si;
+                            s_tile = t;
+                            s_seg = load_task_seg(job->tseg + si);
+                            cmd = 0u;
+                        }
+                        break;
+                    }
+                    if (*(volatile const uint32_t *)&ctl->status != 0u) break;
+                    if (++polls >= spin_limit) { set_status(ctl, TSQS_ETIMEOUT); break; }
+                    __nanosleep(polls < 64 ? 32 : 256);
+                }
+            }
+            s_cmd = cmd;
+        }
+        __syncthreads();
+        if (s_cmd) break;
+
+        // ---- classify.  Thread t holds the 16-byte vectors k * BLOCK + t of the tile.
+        const uint32_t si = s_si;
+        const int64_t sb = (int64_t)s_seg.begin, se = (int64_t)s_seg.end;
+        const uint32_t depth = s_seg.depth, ntiles = s_seg.ntiles;
+        const int64_t t0 = s_seg.s0 + (int64_t)(s_tile - s_seg.tile_begin) * TILE;
+        const C pc = c_from<C>(s_seg.piv_lo, s_seg.piv_hi);
+        const D pd = K::pdom(pc);
+        const S *__restrict__ src = buffer<K>(job, (int)(depth & 1u));
+        S *__restrict__ dst = buffer<K>(job, (int)(depth & 1u) ^ 1);
+        S v[ITEMS];
+        uint32_t ltm = 0, gtm = 0;
+        if (t0 >= sb && t0 + TILE <= se && t0 >= e_lo && t0 + TILE <= e_hi) {
+#pragma unroll
+            for (int k = 0; k < NV; k++) ldcg_vec<S, V>(src + t0 + (k * BLOCK + tid) * V, &v[k * V]);
+#pragma unroll
+            for (int i = 0; i < ITEMS; i++) {
+                const D d = K::dom(v[i]);
+                if (c_lt(d, pd)) ltm |= 1u << i;
+                if (c_lt(pd, d)) gtm |= 1u << i;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                const int64_t vs = t0 + (int64_t)(k * BLOCK + tid) * V;
+                if (vs + V <= sb || vs >= se) continue;
+                if (vs >= e_lo && vs + V <= e_hi) {
+                    ldcg_vec<S, V>(src + vs, &v[k * V]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; j++)
+                        if (vs + j >= sb && vs + j < se) v[k * V + j] = ldcg_key(src + vs + j);
+                }
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    const bool in = vs + j >= sb && vs + j < se;
+                    const D d = K::dom(v[k * V + j]);
+                    ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
+                    gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
+                }
+            }
+        }
+
+        // ---- block offsets, reservation on the segment's cursor, staging
+        const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        const uint32_t ws = lane < NW ? wsum[lane] : 0u;
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, NW - 1);
+        const uint32_t wex = __shfl_sync(0xffffffffu, wi - ws, warp);
+        const uint32_t texcl = wex + inc - cnt;
+        const uint32_t tlt = total & 0xFFFFu, tgt = total >> 16;
+        if (tid == 0)
+            s_resv = atomicAdd(&job->tseg[si].cursor, ((unsigned long long)tgt << 32) | tlt);
+        {
+            const uint32_t b0 = smem_addr(buf), es = (uint32_t)sizeof(S);
+            uint32_t la = b0 + (texcl & 0xFFFFu) * es;
+            uint32_t ga = b0 + ((TILE - 1) - (texcl >> 16)) * es;
+            const uint32_t da = b0 + (uint32_t)TILE * es;
+#pragma unroll
+            for (int k = 0; k < ITEMS; k++) {
+                const bool l = (ltm >> k) & 1u, g = (gtm >> k) & 1u;
+                sts_raw(l ? la : (g ? ga : da), v[k]);
+                la += l ? es : 0u;
+                ga -= g ? es : 0u;
+            }
+        }
+        __syncthreads();               // staged; s_resv ready
+        // ---- write both runs: <p at sb + ex_lt, >p ending at se - ex_gt
+        {
+            const unsigned long long resv = s_resv;
+            const uint64_t ex_lt = resv & 0xFFFFFFFFull, ex_gt = resv >> 32;
+            copy_run<S, V, BLOCK>(dst, (uint64_t)sb + ex_lt, buf, tlt, vec_off);
+            copy_run<S, V, BLOCK>(dst, (uint64_t)se - ex_gt - tgt, buf + (TILE - tgt), tgt, vec_off);
+        }
+        __syncthreads();               // every run written (and buf read) by the block
+        if (tid == 0) {
+            __threadfence();           // release: this tile's runs before its count
+            s_last = atomicAdd(&job->tseg[si].done, 1u) + 1u == ntiles ? 1u : 0u;
+            if (s_last) {
+                __threadfence();       // acquire: every tile's runs and reservation
+                s_resv = ld_relaxed(&job->tseg[si].cursor);
+                s_push[0] = s_push[1] = 0u;
+            }
+        }
+        __syncthreads();
+        if (!s_last) continue;
+
+        // ---- the segment is done: =p run and children (block-uniform from here)
+        const unsigned long long fin = s_resv;
+        const uint64_t nlt = fin & 0xFFFFFFFFull, ngt = fin >> 32;
+        const uint64_t m = (uint64_t)(se - sb);
+        if (nlt + ngt >= m) {
+            // p is an element of the segment, so the =p run is never empty; a violation
+            // means corrupted state: stop instead of looping forever
+            if (tid == 0) set_status(ctl, TSQS_EINTERNAL);
+            continue;
+        }
+        const uint32_t cd = depth + 1u;
+        const int cpar = (int)(cd & 1u);
+        if (warp < 2) {
+            // warp c pushes child c: [sb, sb + #<p) or [se - #>p, se)
+            const uint64_t cb = warp == 0 ? (uint64_t)sb : (uint64_t)se - ngt;
+            const uint64_t ce = warp == 0 ? (uint64_t)sb + nlt : (uint64_t)se;
+            const uint64_t len = ce - cb;
+            if (len > T && cd < job->deep_level) {
+                if (push_task<K>(job, ctl, cb, ce, cd, false) && lane == 0) s_push[warp] = 1u;
+            } else if (len > T) {
+                if (lane == 0) {
+                    // depth guard: the bitonic sorter takes it after this launch
+                    const uint32_t bd = atomicAdd(&ctl->ndeep, 1u);
+                    if (bd >= job->cap_deep) {
+                        set_status(ctl, TSQS_EINTERNAL);
+                    } else {
+                        LeafItem it;
+                        it.begin = cb;
+                        it.len = (uint32_t)len;
+                        it.kind = cpar ? kLeafInAlt : 0u;
+                        it.v_lo = 0;
+                        it.v_hi = 0;
+                        job->deep[bd] = it;
+                    }
+                }
+            } else if (len >= 1 && lane == 0) {
+                push_leaf(job, ctl, cb, ce, cpar);
+            }
+        } else {
+            // the other warps place the =p run: written here up to kTaskInlineFill
+            // elements, else queued as fill items for the leaf pass
+            const uint64_t eqb = (uint64_t)sb + nlt, eqe = (uint64_t)se - ngt;
+            const uint32_t t = (uint32_t)tid - 64u;
+            if (eqe - eqb <= kTaskInlineFill) {
+                fill_span<S, V>(reinterpret_cast<S *>(job->out), eqb, eqe, K::uncanon(pc), vec_off,
+                                t, (uint32_t)BLOCK - 64u);
+                if (t == 0) atomicAdd((unsigned long long *)&ctl->leaf_filled, (unsigned long long)(eqe - eqb));
+            } else if (t == 0) {
+                const uint32_t nch = (uint32_t)((eqe - eqb + kFillChunk - 1) / kFillChunk);
+                const uint32_t bl = atomicAdd(&ctl->nleaf, nch);
+                for (uint32_t c = 0; c < nch; c++) {
+                    if (bl + c >= job->cap_leaves) { set_status(ctl, TSQS_EINTERNAL); break; }
+                    LeafItem li;
+                    li.begin = eqb + (uint64_t)c * kFillChunk;
+                    const uint64_t rest = eqe - li.begin;
+                    li.len = (uint32_t)(rest < kFillChunk ? rest : kFillChunk);
+                    li.kind = LEAF_FILL;
+                    li.v_lo = s_seg.piv_lo;
+                    li.v_hi = s_seg.piv_hi;
+                    job->leaves[bl + c] = li;
+                }
+            }
+        }
+        __syncthreads();
+        // children are published before this segment leaves the live count, so the count
+        // reaches zero only when no segment is pushed or in progress
+        if (tid == 0) {
+            const uint32_t np = s_push[0] + s_push[1];
+            const uint32_t old = atomicAdd(&ctl->live, np - 1u);
+            s_end = old + np - 1u == 0u ? 1u : 0u;
+            if (s_end) {
+                __threadfence();
+                s_ta = *(volatile const uint32_t *)&ctl->talloc;
+            }
+        }
+        __syncthreads();
+        if (s_end) {
+            // every block holds at most one claim past the last tile id
+            const uint32_t ta = s_ta;
+            for (uint32_t g = (uint32_t)tid; g < gridDim.x && (uint64_t)ta + g < job->cap_trow; g += BLOCK)
+                st_relaxed(job->trow + ta + g, kTaskEnd);
+            if (tid == 0 && use_handle) {
+                __threadfence();
+                const bool ok = *(volatile const uint32_t *)&ctl->status == 0u;
+                cudaGraphSetConditional(h_deep, (ok && *(volatile const uint32_t *)&ctl->ndeep != 0u) ? 1u : 0u);
+            }
+        }
+    }
+}
+
+}  // namespace tsqs

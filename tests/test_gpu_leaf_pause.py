@@ -1,7 +1,8 @@
 """The level loop's pause for a leaf pass: with the leaf queue's pause threshold forced
 down, the graph leaves its level loop whenever too many leaf items wait, sorts them,
 and resumes the levels.  Every result must still equal the oracle's (Section III's
-recursion on the two outer parts, in any order)."""
+recursion on the two outer parts, in any order).  The sorts run on contexts whose plan
+asks for the level-by-level schedule (the task-parallel one has no level loop)."""
 import ctypes
 
 import numpy as np
@@ -23,6 +24,13 @@ def T():
     return T
 
 
+def level_ctx(T):
+    p = T.Plan()
+    assert T.lib().tsqs_plan_default(1, 0, ctypes.byref(p)) == 0
+    p.schedule = 1
+    return T.Context(p)
+
+
 @pytest.fixture
 def defer(T):
     def set_defer(items):
@@ -42,7 +50,7 @@ def _oracle(orc, a, kind):
 def test_pause_random_int32(T, orc, defer, items, n):
     defer(items)
     a = int32_pattern("random", n, seed=items + n)
-    ctx = T.Context()
+    ctx = level_ctx(T)
     t = torch.from_numpy(a.copy()).cuda()
     T.sort_(t, kind=1, ctx=ctx)
     torch.cuda.synchronize()
@@ -57,27 +65,31 @@ def test_pause_random_int32(T, orc, defer, items, n):
 def test_pause_patterns(T, orc, defer, pattern):
     defer(2)
     a = int32_pattern(pattern, 500_009, seed=5)
+    ctx = level_ctx(T)
     t = torch.from_numpy(a.copy()).cuda()
-    T.sort_(t, kind=1)
+    T.sort_(t, kind=1, ctx=ctx)
     torch.cuda.synchronize()
-    assert T.last_device_status() == 0
+    assert ctx.status() == 0
     assert t.cpu().numpy().tobytes() == _oracle(orc, a, 1).tobytes()
+    ctx.close()
 
 
 def test_pause_records_floats(T, orc, defer):
     defer(1)
+    ctx = level_ctx(T)
     r = records_u64(200_003, seed=8)
     t = torch.from_numpy(r.view(np.int64).copy()).cuda()
-    T.sort_(t, records=True)
+    T.sort_(t, records=True, ctx=ctx)
     torch.cuda.synchronize()
-    assert T.last_device_status() == 0
+    assert ctx.status() == 0
     assert t.cpu().numpy().view(np.uint64).reshape(-1, 2).tobytes() == _oracle(orc, r, 7).tobytes()
     f = floats_normal_specials(400_001, seed=9)
     t = torch.from_numpy(f.copy()).cuda()
-    T.sort_(t, kind=3)
+    T.sort_(t, kind=3, ctx=ctx)
     torch.cuda.synchronize()
-    assert T.last_device_status() == 0
+    assert ctx.status() == 0
     assert t.cpu().numpy().view(np.float32).tobytes() == _oracle(orc, f, 3).tobytes()
+    ctx.close()
 
 
 def test_pause_segmented_host_and_timed(T, orc, defer):
@@ -86,20 +98,23 @@ def test_pause_segmented_host_and_timed(T, orc, defer):
     sizes = rng.integers(0, 60_000, 80)
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     a = rng.integers(-2**31, 2**31 - 1, int(offs[-1])).astype(np.int32)
+    ctx = level_ctx(T)
     t = torch.from_numpy(a.copy()).cuda()
-    T.sort_segmented_(t, torch.from_numpy(offs).cuda(), kind=1)
+    T.sort_segmented_(t, torch.from_numpy(offs).cuda(), kind=1, ctx=ctx)
     torch.cuda.synchronize()
-    assert T.last_device_status() == 0
+    assert ctx.status() == 0
+    ctx.close()
     exp = a.copy()
     orc.tsqs_sort_segments(exp, offs.astype(np.uint64), 1, threads=4)
     assert t.cpu().numpy().tobytes() == exp.tobytes()
-    # host array, written through the mapped output by the paused graph
+    # host array, written through the mapped output (default context: at this size the
+    # task-parallel schedule)
     b = int32_pattern("random", 1_000_003, seed=22)
     h = torch.from_numpy(b.copy()).pin_memory()
     assert T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), len(b), 4, 1, None) == 0
     assert h.numpy().tobytes() == _oracle(orc, b, 1).tobytes()
     # host-driven run of the same kernels: its per-level leaf launch takes the pause
-    ctx = T.Context()
+    ctx = level_ctx(T)
     c = torch.from_numpy(b.copy()).cuda()
     ms, keys, lms = ctx.sort_timed(c, kind=1)
     torch.cuda.synchronize()

@@ -1,0 +1,227 @@
+"""The task-parallel schedule (k_task: every segment partitioned as soon as its parent is
+done, no level barrier) against the CPU oracle, and against the level-by-level schedule
+of the same kernels' steps (marked gpu).
+
+The sorted output is unique, so both schedules must give the oracle's bytes for every
+key kind, every size class (one tile, a few tiles, a ragged tail, many tiles), long =p
+runs (fill items past the inline bound), presorted roots, many root segments, the depth
+guard taking segments out of the task kernel, and a withheld tile row that must end in
+TSQS_ETIMEOUT through the bounded wait rather than a hang.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import PATTERNS, int32_pattern, records_u64, rand_u64
+from workloads.patterns import batched_segments, batched_keys
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+KINDS = {"i32": (1, np.int32), "u32": (2, np.uint32), "f32": (3, np.float32),
+         "i64": (4, np.int64), "u64": (5, np.uint64), "f64": (6, np.float64)}
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1505_00558_gb300 as T
+    T.lib()
+    return T
+
+
+def _ctx(T, schedule: int):
+    p = T.Plan()
+    assert T.lib().tsqs_plan_default(1, 0, ctypes.byref(p)) == 0
+    p.schedule = schedule
+    return T.Context(p)
+
+
+def _keys(kind_name: str, n: int, seed: int) -> np.ndarray:
+    code, dt = KINDS[kind_name]
+    bits = rand_u64(seed, 200 + code, n)
+    a = (bits >> np.uint64(32)).astype(np.uint32).view(dt) if np.dtype(dt).itemsize == 4 else bits.view(dt)
+    if n > 10:
+        a[::5] = a[1]                                   # one long =p run, spread out
+    if kind_name in ("f32", "f64") and n > 40:
+        sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan], dtype=dt)
+        a[7:7 + 6 * (n // 40)] = np.resize(sp, 6 * (n // 40))
+    return a
+
+
+def _dev(a: np.ndarray):
+    b = np.ascontiguousarray(a)
+    if b.dtype in (np.uint32, np.float32):
+        b = b.view(np.int32)
+    elif b.dtype in (np.uint64, np.float64):
+        b = b.view(np.int64)
+    return torch.from_numpy(b.copy()).cuda()
+
+
+def _oracle(orc, a: np.ndarray, kind: int) -> bytes:
+    b = np.ascontiguousarray(a.copy())
+    orc.tsqs_sort(b, kind)
+    return b.tobytes()
+
+
+def _sort(T, ctx, a: np.ndarray, kind: int) -> bytes:
+    t = _dev(a)
+    T.sort_(t, kind=kind, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == T.TSQS_OK
+    return t.cpu().numpy().tobytes()
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("kind_name", list(KINDS))
+@pytest.mark.parametrize("n", [4097, 5000, 16_385, 65_537, 300_001, 1_000_003])
+def test_both_schedules_match_oracle(T, orc, schedule, kind_name, n):
+    code = KINDS[kind_name][0]
+    a = _keys(kind_name, n, seed=n % 1000 + code)
+    ctx = _ctx(T, schedule)
+    assert _sort(T, ctx, a, code) == _oracle(orc, a, code)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [4097, 70_001, 1_000_003])
+def test_records_task_schedule(T, orc, n):
+    r = records_u64(n, seed=n)
+    ctx = _ctx(T, 2)
+    t = torch.from_numpy(r.view(np.int64).copy()).cuda()
+    T.sort_(t, records=True, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == T.TSQS_OK
+    assert t.cpu().numpy().tobytes() == _oracle(orc, r, 7)
+    ctx.close()
+
+
+@pytest.mark.parametrize("pattern", PATTERNS)
+def test_patterns_default_schedule(T, orc, pattern):
+    """Seven patterns at 2^22 (the task schedule by default): presorted roots, long =p
+    runs (many equals: fill items past the inline bound), organ pipes."""
+    n = 1 << 22
+    a = int32_pattern(pattern, n, seed=11)
+    ctx = T.Context()
+    assert _sort(T, ctx, a, 1) == _oracle(orc, a, 1)
+    st = ctx.stats()
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] + st["presorted_keys"] + st["deep_sorted_keys"] == n
+    ctx.close()
+
+
+def test_few_distinct_values_fill_items(T, orc):
+    """Eight distinct values in 3e6 keys: every =p run is far above the inline fill bound,
+    so the fills go through the leaf pass as queued items."""
+    n = 3_000_000
+    a = (rand_u64(5, 9, n) % np.uint64(8)).astype(np.int32)
+    ctx = _ctx(T, 2)
+    assert _sort(T, ctx, a, 1) == _oracle(orc, a, 1)
+    st = ctx.stats()
+    assert st["leaf_filled_keys"] >= n - 8 * 4096
+    ctx.close()
+
+
+def test_many_root_segments(T, orc):
+    """Root segments of every size class in one call (one warp per root in the task
+    init): empty, one element, below and above the on-chip threshold."""
+    nseg = 3000
+    offs, _, pat = batched_segments(nseg, seed=3, max_log2=16)
+    x = batched_keys(offs, pat, seed=3)
+    exp = x.copy()
+    orc.tsqs_sort_segments(exp, offs, orc.KIND_I32, threads=8)
+    ctx = _ctx(T, 2)
+    t = torch.from_numpy(x.copy()).cuda()
+    d_offs = torch.from_numpy(offs.astype(np.int64)).cuda()
+    T.sort_segmented_(t, d_offs, kind=1, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == T.TSQS_OK
+    assert t.cpu().numpy().tobytes() == exp.tobytes()
+    ctx.close()
+
+
+def test_task_schedule_at_2e25(T, orc):
+    """Schedule 2 past the default bound (2^24): 2^25 keys, a deeper recursion tree."""
+    n = 1 << 25
+    a = int32_pattern("random", n, seed=4)
+    ctx = _ctx(T, 2)
+    assert _sort(T, ctx, a, 1) == _oracle(orc, a, 1)
+    st = ctx.stats()
+    assert st["level_keys"][0] == n and st["levels"] >= 12
+    ctx.close()
+
+
+def test_stats_of_task_schedule(T):
+    n = 1 << 22
+    a = int32_pattern("random", n, seed=3)
+    ctx = T.Context()
+    t = torch.from_numpy(a.copy()).cuda()
+    T.sort_(t, kind=1, ctx=ctx)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert ctx.status() == 0
+    # the root is depth 0; every key is finished by a leaf sort or an =p fill
+    assert st["level_keys"][0] == n and st["levels"] >= 9
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] == n
+    assert st["partition_keys"] == sum(st["level_keys"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("deep", [1, 2, 4])
+def test_depth_guard_in_task_schedule(T, orc, deep):
+    """Children at depth >= the guard's level leave the task kernel for the bitonic
+    sorter (the IF branch the task kernel's last block sets)."""
+    n = 1_500_007
+    a = int32_pattern("random", n, seed=deep)
+    L = T.lib()
+    L.tsqs_debug_set_deep_level(deep)
+    try:
+        ctx = _ctx(T, 2)
+        got = _sort(T, ctx, a, 1)
+        st = ctx.stats()
+        ctx.close()
+    finally:
+        L.tsqs_debug_set_deep_level(0)
+    assert got == _oracle(orc, a, 1)
+    assert st["deep_sorted_keys"] > 0
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] + st["deep_sorted_keys"] == n
+
+
+def test_withheld_rows_end_in_timeout(T):
+    """The first task segment never publishes its tile rows: every block that claimed
+    one of its tiles polls until the spin limit, the sort ends with TSQS_ETIMEOUT, and
+    the next sort on the same context is clean."""
+    n = 200_003
+    a = int32_pattern("random", n, seed=8)
+    L = T.lib()
+    ctx = _ctx(T, 2)
+    L.tsqs_debug_set_spin_limit(2000)
+    L.tsqs_debug_withhold_publish(2)
+    try:
+        t = _dev(a)
+        T.sort_(t, kind=1, ctx=ctx)
+        torch.cuda.synchronize()
+        st = ctx.status()
+    finally:
+        L.tsqs_debug_withhold_publish(0)
+        L.tsqs_debug_set_spin_limit(0)
+    assert st == T.TSQS_ETIMEOUT
+    t = _dev(a)
+    T.sort_(t, kind=1, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert np.array_equal(t.cpu().numpy(), np.sort(a))
+    ctx.close()
+
+
+def test_schedules_agree_on_serving_sizes(T):
+    """Request sizes of the serving mix (2^10 .. 2^22) sorted by both schedules on one
+    stream, back to back: identical output."""
+    rng = np.random.default_rng(1)
+    c1, c2 = _ctx(T, 1), _ctx(T, 2)
+    for lg in range(10, 23, 2):
+        n = int(rng.integers(1 << lg, 2 << lg))
+        a = int32_pattern("random", n, seed=lg)
+        assert _sort(T, c1, a, 1) == _sort(T, c2, a, 1)
+    c1.close()
+    c2.close()
