@@ -143,7 +143,7 @@ Layout make_layout(size_t n, size_t nseg, size_t es, const tsqs_plan &plan, int 
     L.dchunks_off = off;        off = align_up(off + (cf + 1) * sizeof(uint32_t), 256);
     L.misc_off = off;           off = align_up(off + 4096, 256);   // debug buffers
     L.ttask_off = off;          off = align_up(off + cts * sizeof(TaskSeg), 256);
-    L.trow_off = off;           off = align_up(off + ctr * sizeof(uint32_t), 256);
+    L.trow_off = off;           off = align_up(off + ctr * sizeof(unsigned long long), 256);
     L.total = off;
     return L;
 }
@@ -348,7 +348,7 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
     if (task_tile) {
         j->tile = (uint32_t)task_tile;
         j->tseg = (TaskSeg *)(c->scratch + L.ttask_off);
-        j->trow = (uint32_t *)(c->scratch + L.trow_off);
+        j->trow = (unsigned long long *)(c->scratch + L.trow_off);
         j->cap_tseg = L.cap_tseg;
         j->cap_trow = L.cap_trow;
         j->task_grid = (uint32_t)c->task_grid[o->kind];

@@ -22,7 +22,6 @@ constexpr uint32_t kFillChunk = 16384;      // =p fills are split into items of 
 constexpr uint32_t kInlineFill = 16;        // =p runs up to this long are written by the level-end kernel
 constexpr int kMaxSmall = 4096;             // largest on-chip segment
 constexpr int kStatLevels = 64;
-constexpr uint32_t kTaskEnd = 0xFFFFFFFFu;  // tile-row value: no more work
 constexpr uint32_t kTaskGridMax = 4096;     // end-of-work rows reserved past the last tile
 
 
@@ -134,8 +133,8 @@ struct Job {
     uint64_t seed;            // sample jitter seed
     // task schedule (k_task); null / zero when the call runs level by level
     TaskSeg *tseg;            // pushed segments
-    uint32_t *trow;           // tile id -> segment + 1 (0: not pushed yet; kTaskEnd: no more
-                              // work), zeroed by k_orient at the start of every call
+    unsigned long long *trow; // tile id -> (tile origin, buffer, segment), 0 while the
+                              // segment is not pushed (k_orient zeroes the rows of a call)
     uint32_t cap_tseg, cap_trow;
     uint32_t task_grid;       // blocks of k_task (end-of-work rows to write)
     uint32_t pad4;

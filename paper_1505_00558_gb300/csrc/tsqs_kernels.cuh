@@ -374,7 +374,7 @@ __global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
     if (job->trow) {                   // task schedule: this call's tile rows start empty
         const uint32_t stride = gridDim.x * blockDim.x;
         for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < job->cap_trow; i += stride)
-            job->trow[i] = 0u;
+            job->trow[i] = 0ull;
     }
     for (uint64_t s = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
         uint64_t b, e;

@@ -5,10 +5,12 @@
 // whose work is a handful of tiles.  Here the recursion of Section III.F runs without
 // level barriers, in one persistent launch:
 //   - tile ids run over the whole sort and are claimed in one global order; a segment
-//     gets a range of ids when it is pushed, and each id's row (segment index + 1; the
-//     rows are zeroed by the first kernel of the call) is written once the segment's
-//     descriptor and sampled median (Section III.H, V.C) are in memory;
-//   - a block that claimed an id whose row is not written yet polls it (bounded);
+//     gets a range of ids when it is pushed, and each id's row (the tile's first element,
+//     the buffer holding its keys and the segment index; the rows are zeroed by the
+//     first kernel of the call) is written once the segment's descriptor and sampled
+//     median (Section III.H, V.C) are in memory;
+//   - a block that claimed an id whose row is not written yet polls it (bounded); the
+//     row alone lets it start loading the tile while the descriptor is read;
 //   - a tile is classified against p once, its <p and >p elements are packed at the two
 //     ends of the segment through one 64-bit atomic on the segment's cursor (the roles of
 //     the paper's l and r), and the =p elements are never written or compared again;
@@ -28,13 +30,19 @@ namespace tsqs {
 constexpr uint32_t kTaskInlineFill = 1u << 16;   // =p runs up to this long are written by the
                                                  // block that finishes their segment
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+
+// Tile row: [63:32] first element of the tile + kRowBias (tile origins start at most
+// 15 elements below 0, so a written row is never 0), [31] buffer of the keys, [30:0]
+// segment index.  kTaskEndRow: no more work.
+constexpr int64_t kRowBias = 16;
+constexpr unsigned long long kTaskEndRow = ~0ull;
+__device__ __forceinline__ unsigned long long task_row(int64_t t0, uint32_t par, uint32_t si) {
+    return ((unsigned long long)(uint32_t)(t0 + kRowBias) << 32) | ((unsigned long long)par << 31) | si;
 }
 
 // Descriptor of segment si from L2 (it may have been written in this launch after this
@@ -92,15 +100,20 @@ template <class K>
 __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint32_t d,
                           bool withhold) {
     const uint32_t lane = threadIdx.x & 31u;
-    const typename K::C p = sample_pivot<K, true>(buffer<K>(job, (int)(d & 1u)), b, e,
-                                                  job->samples, job->seed, nullptr);
     const int64_t s0 = tile_origin<K::V>(b, job->vec_off);
-    const uint32_t nt = tiles_for(e, s0, (int)job->tile);
+    const int TILE = (int)job->tile;
+    const uint32_t nt = tiles_for(e, s0, TILE);
+    // the table slots first: their round trip overlaps the sample loads
     uint32_t fi = 0, tb = 0, ok = 0;
     if (lane == 0) {
         fi = atomicAdd(&ctl->tsegs, 1u);
         tb = atomicAdd(&ctl->talloc, nt);
-        ok = (fi < job->cap_tseg && (uint64_t)tb + nt + kTaskGridMax <= job->cap_trow) ? 1u : 0u;
+    }
+    const typename K::C p = sample_pivot<K, true>(buffer<K>(job, (int)(d & 1u)), b, e,
+                                                  job->samples, job->seed, nullptr);
+    if (lane == 0) {
+        ok = (fi < job->cap_tseg && fi < 0x80000000u &&
+              (uint64_t)tb + nt + kTaskGridMax <= job->cap_trow) ? 1u : 0u;
         if (ok) {
             TaskSeg ts;
             ts.begin = b;
@@ -113,10 +126,6 @@ __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint
             ts.done = 0u;
             ts.cursor = 0ull;
             job->tseg[fi] = ts;
-            const unsigned long long m = e - b;
-            if (d < (uint32_t)kStatLevels) atomicAdd((unsigned long long *)&ctl->level_keys[d], m);
-            atomicAdd((unsigned long long *)&ctl->partition_keys, m);
-            atomicMax(&ctl->levels_done, d + 1u);
         } else {
             set_status(ctl, TSQS_EINTERNAL);
         }
@@ -129,8 +138,15 @@ __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint
     // ahead of its row stores (a release that covers lane 0's stores)
     __syncwarp();
     __threadfence();
-    if (withhold && fi == 0u) return true;
-    for (uint32_t k = lane; k < nt; k += 32u) st_relaxed(job->trow + tb + k, fi + 1u);
+    if (!(withhold && fi == 0u))
+        for (uint32_t k = lane; k < nt; k += 32u)
+            st_relaxed(job->trow + tb + k, task_row(s0 + (int64_t)k * TILE, d & 1u, fi));
+    if (lane == 0) {                   // statistics, after the rows are out
+        const unsigned long long m = e - b;
+        if (d < (uint32_t)kStatLevels) atomicAdd((unsigned long long *)&ctl->level_keys[d], m);
+        atomicAdd((unsigned long long *)&ctl->partition_keys, m);
+        atomicMax(&ctl->levels_done, d + 1u);
+    }
     return true;
 }
 
@@ -186,7 +202,7 @@ __global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
         if (*(volatile const uint32_t *)&ctl->live == 0u) {
             const uint32_t ta = *(volatile const uint32_t *)&ctl->talloc;
             for (uint32_t g = threadIdx.x; g < job->task_grid && (uint64_t)ta + g < job->cap_trow; g += blockDim.x)
-                st_relaxed(job->trow + ta + g, kTaskEnd);
+                st_relaxed(job->trow + ta + g, kTaskEndRow);
         }
         if (threadIdx.x == 0) ctl->blocks_done = 0u;
     }
@@ -196,7 +212,7 @@ __global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
 // last segment finishes, the block that finished it sets the depth guard's branch
 // (graph launches: use_handle) from the deep queue.
 template <int KIND, int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl *ctl,
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restrict__ job, Ctl *ctl,
                                                 cudaGraphConditionalHandle h_deep, int use_handle) {
     using K = Key<KIND>;
     using S = typename K::S;
@@ -207,7 +223,8 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
     __shared__ __align__(16) S buf[TILE + V];      // staged runs + one dummy 16-byte slot
     __shared__ uint32_t wsum[NW];
     __shared__ TaskSeg s_seg;
-    __shared__ uint32_t s_si, s_tile, s_cmd, s_last, s_push[2], s_end, s_ta;
+    __shared__ unsigned long long s_row;
+    __shared__ uint32_t s_cmd, s_last, s_push[2], s_end, s_ta;
     __shared__ unsigned long long s_resv;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -221,6 +238,7 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
 
     for (;;) {
         // ---- claim the next tile id and wait for its row
+        TaskSeg seg;
         if (tid == 0) {
             uint32_t cmd = 1u;
             const uint32_t t = atomicAdd(&ctl->tclaim, 1u);
@@ -229,20 +247,18 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
             } else {
                 uint32_t polls = 0;
                 for (;;) {
-                    const uint32_t r = ld_acquire(job->trow + t);
-                    if (r != 0u) {
-                        if (r != kTaskEnd) {
-                            const uint32_t si = r - 1u;
-                            s_si = si;
-                            s_tile = t;
-                            s_seg = load_task_seg(job->tseg + si);
+                    const unsigned long long r = ld_acquire(job->trow + t);
+                    if (r != 0ull) {
+                        if (r != kTaskEndRow) {
+                            s_row = r;
+                            seg = load_task_seg(job->tseg + (uint32_t)(r & 0x7FFFFFFFull));
                             cmd = 0u;
                         }
                         break;
                     }
                     if (*(volatile const uint32_t *)&ctl->status != 0u) break;
                     if (++polls >= spin_limit) { set_status(ctl, TSQS_ETIMEOUT); break; }
-                    __nanosleep(polls < 64 ? 32 : 256);
+                    __nanosleep(polls < 256 ? 32 : 128);
                 }
             }
             s_cmd = cmd;
@@ -250,20 +266,45 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
         __syncthreads();
         if (s_cmd) break;
 
-        // ---- classify.  Thread t holds the 16-byte vectors k * BLOCK + t of the tile.
-        const uint32_t si = s_si;
-        const int64_t sb = (int64_t)s_seg.begin, se = (int64_t)s_seg.end;
-        const uint32_t depth = s_seg.depth, ntiles = s_seg.ntiles;
-        const int64_t t0 = s_seg.s0 + (int64_t)(s_tile - s_seg.tile_begin) * TILE;
-        const C pc = c_from<C>(s_seg.piv_lo, s_seg.piv_hi);
-        const D pd = K::pdom(pc);
-        const S *__restrict__ src = buffer<K>(job, (int)(depth & 1u));
-        S *__restrict__ dst = buffer<K>(job, (int)(depth & 1u) ^ 1);
+        // ---- load the tile from the row alone (the descriptor's read is in flight):
+        // thread t holds the 16-byte vectors k * BLOCK + t; every element of the buffer
+        // that the tile covers is read, those outside the segment are masked below
+        const unsigned long long row = s_row;
+        const uint32_t si = (uint32_t)(row & 0x7FFFFFFFull);
+        const int par = (int)((row >> 31) & 1ull);
+        const int64_t t0 = (int64_t)(uint32_t)(row >> 32) - kRowBias;
+        const S *__restrict__ src = buffer<K>(job, par);
+        S *__restrict__ dst = buffer<K>(job, par ^ 1);
         S v[ITEMS];
-        uint32_t ltm = 0, gtm = 0;
-        if (t0 >= sb && t0 + TILE <= se && t0 >= e_lo && t0 + TILE <= e_hi) {
+        if (t0 >= e_lo && t0 + TILE <= e_hi) {
 #pragma unroll
             for (int k = 0; k < NV; k++) ldcg_vec<S, V>(src + t0 + (k * BLOCK + tid) * V, &v[k * V]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                const int64_t vs = t0 + (int64_t)(k * BLOCK + tid) * V;
+                if (vs >= e_lo && vs + V <= e_hi) {
+                    ldcg_vec<S, V>(src + vs, &v[k * V]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; j++)
+                        if (vs + j >= 0 && vs + j < n) v[k * V + j] = ldcg_key(src + vs + j);
+                }
+            }
+        }
+        if (tid == 0) s_seg = seg;
+        __syncthreads();
+
+        // ---- classify against the segment's pivot, inside the segment's bounds
+        const int64_t sb = (int64_t)s_seg.begin, se = (int64_t)s_seg.end;
+        const uint32_t depth = s_seg.depth, ntiles = s_seg.ntiles;
+        // a segment of one tile needs no reservation and no finished-tile count: this
+        // block places its runs at the segment's ends and finishes it
+        const bool single = ntiles == 1u;
+        const C pc = c_from<C>(s_seg.piv_lo, s_seg.piv_hi);
+        const D pd = K::pdom(pc);
+        uint32_t ltm = 0, gtm = 0;
+        if (t0 >= sb && t0 + TILE <= se) {
 #pragma unroll
             for (int i = 0; i < ITEMS; i++) {
                 const D d = K::dom(v[i]);
@@ -274,14 +315,6 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
 #pragma unroll
             for (int k = 0; k < NV; k++) {
                 const int64_t vs = t0 + (int64_t)(k * BLOCK + tid) * V;
-                if (vs + V <= sb || vs >= se) continue;
-                if (vs >= e_lo && vs + V <= e_hi) {
-                    ldcg_vec<S, V>(src + vs, &v[k * V]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < V; j++)
-                        if (vs + j >= sb && vs + j < se) v[k * V + j] = ldcg_key(src + vs + j);
-                }
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     const bool in = vs + j >= sb && vs + j < se;
@@ -313,7 +346,7 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
         const uint32_t wex = __shfl_sync(0xffffffffu, wi - ws, warp);
         const uint32_t texcl = wex + inc - cnt;
         const uint32_t tlt = total & 0xFFFFu, tgt = total >> 16;
-        if (tid == 0)
+        if (tid == 0 && !single)
             s_resv = atomicAdd(&job->tseg[si].cursor, ((unsigned long long)tgt << 32) | tlt);
         {
             const uint32_t b0 = smem_addr(buf), es = (uint32_t)sizeof(S);
@@ -331,17 +364,23 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
         __syncthreads();               // staged; s_resv ready
         // ---- write both runs: <p at sb + ex_lt, >p ending at se - ex_gt
         {
-            const unsigned long long resv = s_resv;
+            const unsigned long long resv = single ? 0ull : s_resv;
             const uint64_t ex_lt = resv & 0xFFFFFFFFull, ex_gt = resv >> 32;
             copy_run<S, V, BLOCK>(dst, (uint64_t)sb + ex_lt, buf, tlt, vec_off);
             copy_run<S, V, BLOCK>(dst, (uint64_t)se - ex_gt - tgt, buf + (TILE - tgt), tgt, vec_off);
         }
         __syncthreads();               // every run written (and buf read) by the block
-        if (tid == 0) {
-            __threadfence();           // release: this tile's runs before its count
-            s_last = atomicAdd(&job->tseg[si].done, 1u) + 1u == ntiles ? 1u : 0u;
+        if (single) {
+            if (tid == 0) {
+                s_last = 1u;
+                s_resv = ((unsigned long long)tgt << 32) | tlt;
+                s_push[0] = s_push[1] = 0u;
+            }
+        } else if (tid == 0) {
+            // release this tile's runs with its count; the last count acquires every
+            // other tile's runs and reservation
+            s_last = atom_add_acq_rel(&job->tseg[si].done, 1u) + 1u == ntiles ? 1u : 0u;
             if (s_last) {
-                __threadfence();       // acquire: every tile's runs and reservation
                 s_resv = ld_relaxed(&job->tseg[si].cursor);
                 s_push[0] = s_push[1] = 0u;
             }
@@ -429,7 +468,7 @@ __global__ void __launch_bounds__(BLOCK) k_task(const Job *__restrict__ job, Ctl
             // every block holds at most one claim past the last tile id
             const uint32_t ta = s_ta;
             for (uint32_t g = (uint32_t)tid; g < gridDim.x && (uint64_t)ta + g < job->cap_trow; g += BLOCK)
-                st_relaxed(job->trow + ta + g, kTaskEnd);
+                st_relaxed(job->trow + ta + g, kTaskEndRow);
             if (tid == 0 && use_handle) {
                 __threadfence();
                 const bool ok = *(volatile const uint32_t *)&ctl->status == 0u;

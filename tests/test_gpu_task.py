@@ -225,3 +225,22 @@ def test_schedules_agree_on_serving_sizes(T):
         assert _sort(T, c1, a, 1) == _sort(T, c2, a, 1)
     c1.close()
     c2.close()
+
+
+@pytest.mark.parametrize("threshold", [512, 1024, 2048])
+@pytest.mark.parametrize("kind_name", ["i32", "f64"])
+def test_single_tile_segments(T, orc, threshold, kind_name):
+    """An on-chip threshold below the task tile: segments that fit in one tile are
+    partitioned and finished by one block, with no reservation and no tile count."""
+    code = KINDS[kind_name][0]
+    n = 400_009
+    a = _keys(kind_name, n, seed=threshold + code)
+    p = T.Plan()
+    assert T.lib().tsqs_plan_default(code, 0, ctypes.byref(p)) == 0
+    p.schedule = 2
+    p.small_threshold = threshold
+    ctx = T.Context(p)
+    assert _sort(T, ctx, a, code) == _oracle(orc, a, code)
+    st = ctx.stats()
+    assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] == n
+    ctx.close()
