@@ -201,13 +201,17 @@ int tsqs_ctx_sort_segmented(tsqs_ctx *ctx, void *base, size_t nmemb_total,
  * paper's qsort-replacement call of the abstract and Section VII, issued as one CUDA
  * graph).  graph_exec points to a cudaGraphExec_t passed as void*:
  *   *graph_exec == NULL  the call builds the whole segmented sort of these arguments as
- *                        one graph (the per-call setup kernel, then the presortedness
- *                        kernels, the conditional level loop, the leaf pass and the depth
- *                        guard), instantiates it into *graph_exec and launches it on
- *                        `stream`;
+ *                        one graph (the per-call setup kernel, then the sort's nodes),
+ *                        instantiates it into *graph_exec and launches it on `stream`;
  *   otherwise            *graph_exec must come from an earlier call with the same ctx and
  *                        key_kind (else TSQS_EINVAL): its setup node is updated to these
- *                        arguments and it is launched.
+ *                        arguments and it is launched.  A call whose size takes the other
+ *                        schedule of the ctx's plan (tsqs_plan.schedule: task-parallel up
+ *                        to 2^24 elements by default, level by level above) releases that
+ *                        graph, builds the other one and stores its new handle in
+ *                        *graph_exec.
+ * The graph holds the same nodes as the ctx's own sort for that size: presortedness, then
+ * the task kernel or the conditional level loop, the leaf pass and the depth guard.
  * d_seg_offsets == NULL sorts base[0, nmemb_total) as one segment; otherwise as
  * tsqs_ctx_sort_segmented.  Nothing to sort (no segment, or one segment of <= 1
  * element) returns TSQS_OK with no graph made.  The caller may also replay the graph

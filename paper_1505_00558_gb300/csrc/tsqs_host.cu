@@ -207,7 +207,7 @@ struct tsqs_ctx {
     size_t item_status_cap = 0;
     // caller-held graphs (tsqs_graph_sort_segmented): each exec with its graph, the
     // setup node whose Job argument a later call updates, and its key kind
-    struct Held { cudaGraphExec_t exec; cudaGraph_t graph; cudaGraphNode_t setup; int kind; };
+    struct Held { cudaGraphExec_t exec; cudaGraph_t graph; cudaGraphNode_t setup; int kind; bool task; };
     std::vector<Held> held;
     std::recursive_mutex mu;
 };
@@ -535,7 +535,7 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
 //     orient -> check -> presort -> task init -> task kernel -> leaf pass
 //       -> IF (some segment reached the depth guard) { deep branch }
 // The task kernel's last block sets the IF condition.
-int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g) {
+int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep = nullptr) {
     Job *pj = c->d_job;
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
@@ -545,7 +545,7 @@ int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g) {
     kp.gridDim = dim3(c->sms * 4);
     kp.blockDim = dim3(256);
     kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_ori, g, nullptr, 0, &kp));
+    CK(cudaGraphAddKernelNode(&n_ori, g, dep, dep ? 1 : 0, &kp));
     kp.func = (void *)o->k_check;
     CK(cudaGraphAddKernelNode(&n_chk, g, &n_ori, 1, &kp));
     kp.func = (void *)o->k_presort;
@@ -828,8 +828,9 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     if ((rc = ctx_init_device(c))) return rc;
     if ((rc = ctx_kind_setup(c, o))) return rc;
     if ((rc = ctx_ensure_scratch(c, o, nmemb_total, offs ? nseg : 1))) return rc;
+    const bool task = task_schedule(c->plan, nmemb_total);
     Job j;
-    if ((rc = make_job(c, o, base, nmemb_total, offs, offs ? nseg : 1, &j))) return rc;
+    if ((rc = make_job(c, o, base, nmemb_total, offs, offs ? nseg : 1, &j, task))) return rc;
     Job *pj = c->d_job;
     Ctl *pc = c->d_ctl;
     void *args[] = {&pj, &pc, &j};
@@ -838,12 +839,23 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(256);
     kp.kernelParams = args;
+    if (h && h->task != task) {
+        // this size takes the other schedule: the graph is rebuilt under a new handle
+        ctx_quiesce(c);
+        cudaGraphExecDestroy(h->exec);
+        cudaGraphDestroy(h->graph);
+        c->held.erase(c->held.begin() + (h - c->held.data()));
+        h = nullptr;
+        *graph_exec = nullptr;
+    }
     if (!h) {
         tsqs_ctx::Held nh{};
         nh.kind = key_kind;
+        nh.task = task;
         CK(cudaGraphCreate(&nh.graph, 0));
         rc = cudaGraphAddKernelNode(&nh.setup, nh.graph, nullptr, 0, &kp) == cudaSuccess
-                 ? build_sort_nodes(c, o, nh.graph, &nh.setup) : TSQS_ECUDA;
+                 ? (task ? build_task_nodes(c, o, nh.graph, &nh.setup) : build_sort_nodes(c, o, nh.graph, &nh.setup))
+                 : TSQS_ECUDA;
         if (rc == TSQS_OK && cudaGraphInstantiate(&nh.exec, nh.graph, 0) != cudaSuccess) rc = TSQS_ECUDA;
         if (rc) {
             cudaGetLastError();

@@ -109,3 +109,36 @@ def test_graph_single_segment_kinds(T, orc):
     orc.tsqs_sort(expc, orc.KIND_I32)
     assert tc.cpu().numpy().tobytes() == expc.tobytes()
     ctx.close()                                   # releases both graphs
+
+
+def test_graph_follows_the_schedule_bound(T, orc):
+    """A held graph is built for the schedule its size takes (task-parallel up to 2^24
+    elements by default): a later call across the bound releases it and returns the
+    other graph's handle; direct replays of either give the oracle's result."""
+    ctx = T.Context()
+    small = int32_pattern("random", 200_003, seed=31)
+    t = torch.from_numpy(small.copy()).cuda()
+    h1 = ctx.graph_sort_segmented(t, None, kind=T.TSQS_I32)
+    assert h1 and ctx.status() == T.TSQS_OK
+    exp_small = small.copy()
+    orc.tsqs_sort(exp_small, orc.KIND_I32)
+    assert t.cpu().numpy().tobytes() == exp_small.tobytes()
+    t.copy_(torch.from_numpy(small))
+    s = torch.cuda.current_stream()
+    assert _cudart().cudaGraphLaunch(ctypes.c_void_p(h1), ctypes.c_void_p(s.cuda_stream)) == 0
+    torch.cuda.synchronize()
+    assert ctx.status() == T.TSQS_OK
+    assert t.cpu().numpy().tobytes() == exp_small.tobytes()
+    # past the bound: the level-by-level graph under a new handle
+    big = torch.from_numpy(int32_pattern("random", (1 << 24) + 4099, seed=32)).cuda()
+    ref = torch.sort(big)[0]
+    h2 = ctx.graph_sort_segmented(big, None, h1, kind=T.TSQS_I32)
+    assert h2 and ctx.status() == T.TSQS_OK
+    assert torch.equal(big, ref)
+    # and back below it
+    t2 = torch.from_numpy(small.copy()).cuda()
+    h3 = ctx.graph_sort_segmented(t2, None, h2, kind=T.TSQS_I32)
+    assert h3 and ctx.status() == T.TSQS_OK
+    assert t2.cpu().numpy().tobytes() == exp_small.tobytes()
+    ctx.graph_destroy(h3)
+    ctx.close()
