@@ -367,7 +367,9 @@ typedef struct {
 } tsqs_result;
 
 /* mem_budget_bytes bounds the device scratch plus in-flight request bytes;
- * n_streams launches may be in flight at once; max_batch bounds requests per launch. */
+ * n_streams launches may be in flight at once; max_batch bounds requests per launch.
+ * Every lane sorts with the level-by-level schedule (tsqs_plan.schedule 1): its launches
+ * interleave with the other lanes' on the GPU. */
 tsqs_server *tsqs_server_create(size_t mem_budget_bytes, int n_streams, int max_batch);
 /* Queues a request on d_base (device, caller-owned, must stay valid until done).
  * Returns TSQS_ENOMEM if the request alone can never fit the budget. */

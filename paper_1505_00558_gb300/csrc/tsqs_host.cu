@@ -351,7 +351,12 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
         j->trow = (unsigned long long *)(c->scratch + L.trow_off);
         j->cap_tseg = L.cap_tseg;
         j->cap_trow = L.cap_trow;
-        j->task_grid = (uint32_t)c->task_grid[o->kind];
+        // blocks that take part: as many as the tiles one depth can hold at once (the keys'
+        // tiles plus two partial tiles per segment), at most the launched grid; the others
+        // return at once and leave their SMs to other streams' work
+        const size_t T = eff_threshold(c->plan, o->leaf_max);
+        const size_t want = n / (size_t)task_tile + 2 * (n / (T + 1)) + 8;
+        j->task_grid = (uint32_t)std::min<size_t>(want, (size_t)c->task_grid[o->kind]);
     }
     return TSQS_OK;
 }

@@ -136,7 +136,8 @@ struct Job {
     unsigned long long *trow; // tile id -> (tile origin, buffer, segment), 0 while the
                               // segment is not pushed (k_orient zeroes the rows of a call)
     uint32_t cap_tseg, cap_trow;
-    uint32_t task_grid;       // blocks of k_task (end-of-work rows to write)
+    uint32_t task_grid;       // blocks of k_task that take part (the rest return at once;
+                              // one end-of-work row each)
     uint32_t pad4;
     // step-level test hooks
     const void *dbg_pivots;   // debug partition: pivots of the given segments

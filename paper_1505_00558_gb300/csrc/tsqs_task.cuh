@@ -235,6 +235,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
     const int64_t e_hi = n - ((n + (int64_t)vec_off) % V);
     const uint64_t T = job->small_T;
     const uint32_t spin_limit = job->spin_limit;
+    // blocks past the ones this input can use leave at once (their SMs go to other work)
+    const uint32_t active = min(gridDim.x, job->task_grid);
+    if (blockIdx.x >= active) return;
 
     for (;;) {
         // ---- claim the next tile id and wait for its row
@@ -465,9 +468,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
         }
         __syncthreads();
         if (s_end) {
-            // every block holds at most one claim past the last tile id
+            // every taking-part block holds at most one claim past the last tile id
             const uint32_t ta = s_ta;
-            for (uint32_t g = (uint32_t)tid; g < gridDim.x && (uint64_t)ta + g < job->cap_trow; g += BLOCK)
+            for (uint32_t g = (uint32_t)tid; g < active && (uint64_t)ta + g < job->cap_trow; g += BLOCK)
                 st_relaxed(job->trow + ta + g, kTaskEndRow);
             if (tid == 0 && use_handle) {
                 __threadfence();
