@@ -2,10 +2,15 @@
 //
 // A context owns one block of device scratch (the second buffer of the ping-pong,
 // the work queues and the look-back words; the analogue of the persistent temporary
-// storage of Section III.G) and one CUDA graph per key kind.  The graph is
-//     orient -> check -> presort -> init
-//       -> while (frontier not empty) { leaf ; pivot ; partition ; level end }
-//       -> final leaf pass   ||   deep prep -> deep tiles -> while (stages) { deep stage } -> deep finish
+// storage of Section III.G) and two CUDA graphs per key kind.  The level-by-level one is
+//     orient -> if (a root is a candidate) { check -> presort } -> init
+//       -> while (levels remain) { while (frontier not empty) { pivot ; partition ; level end } ;
+//                                  leaf pass ; control }
+//       -> if (a segment reached the depth bound) { deep prep -> deep tiles -> while (stages)
+//                                                   { deep stage } -> deep finish }
+// and the task-parallel one (inputs up to a size bound)
+//     orient -> check -> presort -> task init -> task kernel -> leaf pass
+//       -> if (a segment reached the depth bound) { the same deep branch }
 // with the loop conditions set on the device (by the level-end and deep-stage kernels),
 // so a whole sort is one graph launch with no host round trip between levels.  Every kernel reads the
 // per-call description (Job) from device memory, written by a one-thread setup kernel
@@ -364,6 +369,43 @@ int make_job(tsqs_ctx *c, const KindOps *o, void *base, size_t n, const uint64_t
 int add_deep_branch(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, cudaGraphNode_t after,
                     cudaGraphConditionalHandle h_if);
 
+// Adds the presortedness nodes to graph g after `dep` (nullptr: none): the orientation
+// kernel, then IF (it flagged a candidate) { full check ; finishing pass }.  *last is the
+// node the sort's next node depends on.
+int add_presort_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep,
+                      cudaGraphNode_t *last) {
+    Job *pj = c->d_job;
+    Ctl *pc = c->d_ctl;
+    void *args2[] = {&pj, &pc};
+    cudaGraphConditionalHandle h_pre;
+    CK(cudaGraphConditionalHandleCreate(&h_pre, g, 0, cudaGraphCondAssignDefault));
+    void *argso[] = {&pj, &pc, &h_pre};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)o->k_orient_if;
+    kp.gridDim = dim3(c->sms * 4);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = argso;
+    cudaGraphNode_t n_ori, n_if, n_chk, n_pre;
+    CK(cudaGraphAddKernelNode(&n_ori, g, dep, dep ? 1 : 0, &kp));
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_pre;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    CK(cudaGraphAddNode(&n_if, g, &n_ori, nullptr, 1, &ip));
+    cudaGraph_t body = ip.conditional.phGraph_out[0];
+    kp = cudaKernelNodeParams{};
+    kp.func = (void *)o->k_check;
+    kp.gridDim = dim3(c->sms * 4);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args2;
+    CK(cudaGraphAddKernelNode(&n_chk, body, nullptr, 0, &kp));
+    kp.func = (void *)o->k_presort;
+    CK(cudaGraphAddKernelNode(&n_pre, body, &n_chk, 1, &kp));
+    *last = n_if;
+    return TSQS_OK;
+}
+
 // Adds the nodes of one whole sort of kind o to graph g, the first of them depending on
 // `dep` (nullptr: none).  Every kernel reads the per-call Job from c->d_job.
 int build_sort_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep) {
@@ -372,21 +414,15 @@ int build_sort_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
 
-    // presortedness: sample orientation, full check of the candidates, finish them
+    // presortedness: sample orientation; full check and finish only for candidates
+    cudaGraphNode_t n_pre, n_init;
+    int rc = add_presort_nodes(c, o, g, dep, &n_pre);
+    if (rc) return rc;
     cudaKernelNodeParams kp{};
-    cudaGraphNode_t n_ori, n_chk, n_pre, n_init;
-    kp.func = (void *)o->k_orient;
-    kp.gridDim = dim3(c->sms * 4);
-    kp.blockDim = dim3(256);
-    kp.kernelParams = args2;
-    CK(cudaGraphAddKernelNode(&n_ori, g, dep, dep ? 1 : 0, &kp));
-    kp.func = (void *)o->k_check;
-    kp.gridDim = dim3(c->sms * 4);
-    CK(cudaGraphAddKernelNode(&n_chk, g, &n_ori, 1, &kp));
-    kp.func = (void *)o->k_presort;
-    CK(cudaGraphAddKernelNode(&n_pre, g, &n_chk, 1, &kp));
     kp.func = (void *)o->k_init;
     kp.gridDim = dim3(c->sms * 2);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_init, g, &n_pre, 1, &kp));
 
     // outer loop: { level loop ; leaf pass ; control }.  The level loop pauses only when
@@ -544,6 +580,8 @@ int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     Job *pj = c->d_job;
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
+    // presortedness as a plain chain: at the sizes this graph serves, an IF node around the
+    // check and finishing passes costs more than their two launches that return at once
     cudaKernelNodeParams kp{};
     cudaGraphNode_t n_ori, n_chk, n_pre, n_init, n_task, n_leaf;
     kp.func = (void *)o->k_orient;

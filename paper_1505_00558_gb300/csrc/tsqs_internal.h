@@ -165,7 +165,7 @@ struct KindOps {
     int leaf_max;             // largest segment the leaf kernel sorts (32 x keys per lane)
     PartVariant part[kPartVariants];   // [0] is the default shape
     const void *k_init, *k_leaf, *k_pivot, *k_finish;
-    const void *k_orient, *k_check, *k_presort;
+    const void *k_orient, *k_orient_if, *k_check, *k_presort;
     const void *k_deep_prep, *k_deep_tiles, *k_deep_stage, *k_deep_finish;
     int deep_smem;            // dynamic shared memory of the on-chip deep stages
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;

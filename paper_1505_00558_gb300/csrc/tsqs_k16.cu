@@ -34,6 +34,7 @@ KindOps make_ops() {
     o.part[3] = part_variant<KIND, 256, 4, 3>();
     o.k_init = (const void *)k_init<KIND>;
     o.k_orient = (const void *)k_orient<KIND>;
+    o.k_orient_if = (const void *)k_orient_if<KIND>;
     o.k_check = (const void *)k_check<KIND>;
     o.k_presort = (const void *)k_presort<KIND>;
     o.k_deep_prep = (const void *)k_deep_prep<KIND>;

@@ -363,8 +363,12 @@ __device__ __forceinline__ uint64_t root_of(const Job *job, uint64_t x) {
     return lo;
 }
 
+// Orientation samples of every root segment (and the task schedule's row reset).  In a
+// graph (use_handle) a flagged segment also sets the IF node that runs the full check
+// and the finishing pass; with no candidate both are skipped.
 template <int KIND>
-__global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
+__device__ __forceinline__ void orient_body(const Job *__restrict__ job, Ctl *ctl,
+                                            cudaGraphConditionalHandle handle, bool use_handle) {
     using K = Key<KIND>;
     using C = typename K::C;
     const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
@@ -393,8 +397,19 @@ __global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
         if (lane == 0) {
             job->presort[s] = flag;
             if (flag) atomicOr(&ctl->presort_any, 1u);
+            if (flag && use_handle) cudaGraphSetConditional(handle, 1u);
         }
     }
+}
+
+template <int KIND>
+__global__ void k_orient(const Job *__restrict__ job, Ctl *ctl) {
+    orient_body<KIND>(job, ctl, 0, false);
+}
+
+template <int KIND>
+__global__ void k_orient_if(const Job *__restrict__ job, Ctl *ctl, cudaGraphConditionalHandle handle) {
+    orient_body<KIND>(job, ctl, handle, true);
 }
 
 // Clears the flag of every candidate segment that has an adjacent pair out of order.
