@@ -57,12 +57,23 @@ __device__ __forceinline__ TaskSeg load_task_seg(const TaskSeg *p) {
     t.piv_lo = w1.y;
     t.piv_hi = w2.x;
     t.tile_begin = (uint32_t)w2.y;
-    t.ntiles = (uint32_t)(w2.y >> 32);
-    t.depth = (uint32_t)w3.x;
-    t.done = (uint32_t)(w3.x >> 32);
+    t.ntiles_depth = (uint32_t)(w2.y >> 32);
+    t.done = w3.x;
     t.cursor = w3.y;
     return t;
 }
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+// Finished-tile word: the tile count above bit 44; below 2^22 elements a segment's tiles
+// also add their (#<p, #>p), so the last one reads the totals from its own atomic.
+constexpr int kDoneTiles = 44, kDoneCount = 22;
+constexpr uint64_t kDoneSmall = 1ull << kDoneCount;
+constexpr unsigned long long kDoneMask = (1ull << kDoneCount) - 1ull;
 
 // 16-byte L2 load of V storage elements (address 16-byte aligned).
 template <class S, int V>
@@ -112,7 +123,7 @@ __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint
     const typename K::C p = sample_pivot<K, true>(buffer<K>(job, (int)(d & 1u)), b, e,
                                                   job->samples, job->seed, nullptr);
     if (lane == 0) {
-        ok = (fi < job->cap_tseg && fi < 0x80000000u &&
+        ok = (fi < job->cap_tseg && fi < 0x80000000u && nt < (1u << 20) && d < 256u &&
               (uint64_t)tb + nt + kTaskGridMax <= job->cap_trow) ? 1u : 0u;
         if (ok) {
             TaskSeg ts;
@@ -121,9 +132,8 @@ __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint
             ts.s0 = s0;
             c_words(p, ts.piv_lo, ts.piv_hi);
             ts.tile_begin = tb;
-            ts.ntiles = nt;
-            ts.depth = d;
-            ts.done = 0u;
+            ts.ntiles_depth = nt | (d << 24);
+            ts.done = 0ull;
             ts.cursor = 0ull;
             job->tseg[fi] = ts;
         } else {
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
 
         // ---- classify against the segment's pivot, inside the segment's bounds
         const int64_t sb = (int64_t)s_seg.begin, se = (int64_t)s_seg.end;
-        const uint32_t depth = s_seg.depth, ntiles = s_seg.ntiles;
+        const uint32_t depth = s_seg.ntiles_depth >> 24, ntiles = s_seg.ntiles_depth & 0xFFFFFFu;
         // a segment of one tile needs no reservation and no finished-tile count: this
         // block places its runs at the segment's ends and finishes it
         const bool single = ntiles == 1u;
@@ -382,9 +392,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
         } else if (tid == 0) {
             // release this tile's runs with its count; the last count acquires every
             // other tile's runs and reservation
-            s_last = atom_add_acq_rel(&job->tseg[si].done, 1u) + 1u == ntiles ? 1u : 0u;
+            const bool small = (uint64_t)(se - sb) < kDoneSmall;
+            const unsigned long long add = (1ull << kDoneTiles) |
+                (small ? (((unsigned long long)tlt << kDoneCount) | tgt) : 0ull);
+            const unsigned long long old = atom_add_acq_rel(&job->tseg[si].done, add);
+            s_last = (uint32_t)(old >> kDoneTiles) + 1u == ntiles ? 1u : 0u;
             if (s_last) {
-                s_resv = ld_relaxed(&job->tseg[si].cursor);
+                const unsigned long long fin = old + add;
+                s_resv = small ? ((((fin >> kDoneCount) & kDoneMask)) | ((fin & kDoneMask) << 32))
+                               : ld_relaxed(&job->tseg[si].cursor);
                 s_push[0] = s_push[1] = 0u;
             }
         }

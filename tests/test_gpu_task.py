@@ -244,3 +244,26 @@ def test_single_tile_segments(T, orc, threshold, kind_name):
     st = ctx.stats()
     assert st["leaf_sorted_keys"] + st["leaf_filled_keys"] == n
     ctx.close()
+
+
+def test_concurrent_task_sorts_on_four_streams(T, orc):
+    """Four contexts, four streams, four task-parallel sorts in flight at once (each
+    kernel's blocks poll only their own sort's rows): every result equals the oracle's."""
+    sizes = [1_000_003, 300_007, 2_000_001, 65_537]
+    arrays = [int32_pattern("random", n, seed=40 + i) for i, n in enumerate(sizes)]
+    ctxs = [_ctx(T, 2) for _ in sizes]
+    streams = [torch.cuda.Stream() for _ in sizes]
+    ts = [torch.from_numpy(a.copy()).cuda() for a in arrays]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for t, a in zip(ts, arrays):
+            t.copy_(torch.from_numpy(a))
+        torch.cuda.synchronize()
+        for t, c, s in zip(ts, ctxs, streams):
+            T.sort_(t, kind=1, ctx=c, stream=s)
+        torch.cuda.synchronize()
+        for t, a, c in zip(ts, arrays, ctxs):
+            assert c.status() == T.TSQS_OK
+            assert t.cpu().numpy().tobytes() == _oracle(orc, a, 1)
+    for c in ctxs:
+        c.close()
