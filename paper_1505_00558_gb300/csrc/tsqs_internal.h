@@ -86,6 +86,7 @@ struct Ctl {
     uint32_t talloc;          // task schedule: tile ids given to pushed segments
     uint32_t tsegs;           // task schedule: segments pushed
     uint32_t live;            // task schedule: pushed segments not yet finished
+    uint32_t coop_count, coop_gen, coop_go;   // grid barrier of the cooperative deep kernel
     uint64_t front_keys[2];
     uint64_t partition_keys;
     uint64_t leaf_sorted, leaf_filled, leaf_items;
@@ -166,7 +167,7 @@ struct KindOps {
     PartVariant part[kPartVariants];   // [0] is the default shape
     const void *k_init, *k_leaf, *k_pivot, *k_finish;
     const void *k_orient, *k_orient_if, *k_check, *k_presort;
-    const void *k_deep_prep, *k_deep_tiles, *k_deep_stage, *k_deep_finish;
+    const void *k_deep_prep, *k_deep_tiles, *k_deep_stage, *k_deep_finish, *k_deep_all;
     int deep_smem;            // dynamic shared memory of the on-chip deep stages
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
     const void *k_task_init, *k_task;   // task schedule

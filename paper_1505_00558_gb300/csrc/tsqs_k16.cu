@@ -41,6 +41,7 @@ KindOps make_ops() {
     o.k_deep_tiles = (const void *)k_deep_tiles<KIND>;
     o.k_deep_stage = (const void *)k_deep_stage<KIND>;
     o.k_deep_finish = (const void *)k_deep_finish<KIND>;
+    o.k_deep_all = (const void *)k_deep_all<KIND>;
     o.deep_smem = (int)((kDeepTile + kDeepTile / kPadGroup<typename Key<KIND>::C>) * sizeof(typename Key<KIND>::C));
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 2>;
     o.k_pivot = (const void *)k_pivot<KIND>;

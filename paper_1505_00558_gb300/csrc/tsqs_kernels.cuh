@@ -1869,11 +1869,10 @@ __device__ __forceinline__ uint32_t deep_find(const uint32_t *pre, uint32_t nd, 
 }
 
 // One block: prefix sums of the deep segments' tiles and global-stage pair chunks, and
-// the first stage.
-template <int KIND>
-__global__ void k_deep_prep(const Job *__restrict__ job, Ctl *ctl, cudaGraphConditionalHandle h,
-                            int use_handle) {
+// the first stage.  Returns (thread 0) whether any global stage follows.
+__device__ __forceinline__ uint32_t deep_prep_body(const Job *__restrict__ job, Ctl *ctl) {
     __shared__ uint32_t s_t[kDeepThreads], s_c[kDeepThreads], s_l[kDeepThreads];
+    uint32_t cont = 0;
     const uint32_t nd = min(ctl->ndeep, job->cap_deep);
     const uint32_t t = threadIdx.x, per = (nd + blockDim.x - 1) / blockDim.x;
     const uint32_t a = min(nd, t * per), b = min(nd, a + per);
@@ -1900,9 +1899,8 @@ __global__ void k_deep_prep(const Job *__restrict__ job, Ctl *ctl, cudaGraphCond
         ctl->deep_kk = 13u;                                // first merge above one tile
         ctl->deep_jj = 12u;                                // its mirror stage (stride 2^12)
         ctl->deep_blocks = 0u;
-        const uint32_t cont = (nd > 0u && al >= 13u && ctl->status == 0u) ? 1u : 0u;
+        cont = (nd > 0u && al >= 13u && ctl->status == 0u) ? 1u : 0u;
         ctl->deep_cont = cont;
-        if (use_handle) cudaGraphSetConditional(h, cont);
     }
     __syncthreads();
     uint32_t at = s_t[t], ac = s_c[t];
@@ -1913,6 +1911,14 @@ __global__ void k_deep_prep(const Job *__restrict__ job, Ctl *ctl, cudaGraphCond
         at += (uint32_t)((len + kDeepTile - 1) / kDeepTile);
         ac += (uint32_t)(((1ull << deep_log2(len)) / 2 + kDeepChunk - 1) / kDeepChunk);
     }
+    return cont;
+}
+
+template <int KIND>
+__global__ void k_deep_prep(const Job *__restrict__ job, Ctl *ctl, cudaGraphConditionalHandle h,
+                            int use_handle) {
+    const uint32_t cont = deep_prep_body(job, ctl);
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, cont);
 }
 
 // Shared-memory bitonic steps on one 4096-element tile (padded layout, +inf beyond cnt):
@@ -1959,13 +1965,8 @@ __device__ __forceinline__ void deep_tile(const Job *job, const LeafItem &it, ui
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kDeepThreads) k_deep_tiles(const Job *__restrict__ job, Ctl *ctl) {
-    using C = typename Key<KIND>::C;
-    extern __shared__ __align__(16) unsigned char deep_raw[];
-    C *sm = reinterpret_cast<C *>(deep_raw);
-    __shared__ uint32_t s_seg;
-    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
-    if (nd == 0u) return;
+__device__ __forceinline__ void deep_tiles_body(const Job *__restrict__ job, uint32_t nd,
+                                                typename Key<KIND>::C *sm, uint32_t &s_seg) {
     const uint32_t total = job->deep_tiles[nd];
     for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
         if (threadIdx.x == 0) s_seg = deep_find(job->deep_tiles, nd, t);
@@ -1976,19 +1977,30 @@ __global__ void __launch_bounds__(kDeepThreads) k_deep_tiles(const Job *__restri
     }
 }
 
-// One stage for every deep segment whose padded length reaches the current merge width;
-// the last block to finish advances the stage and sets the loop condition.
 template <int KIND>
-__global__ void __launch_bounds__(kDeepThreads) k_deep_stage(const Job *__restrict__ job, Ctl *ctl,
-                                                             cudaGraphConditionalHandle h, int use_handle) {
-    using K = Key<KIND>;
-    using C = typename K::C;
-    using S = typename K::S;
+__global__ void __launch_bounds__(kDeepThreads) k_deep_tiles(const Job *__restrict__ job, Ctl *ctl) {
+    using C = typename Key<KIND>::C;
     extern __shared__ __align__(16) unsigned char deep_raw[];
-    C *sm = reinterpret_cast<C *>(deep_raw);
     __shared__ uint32_t s_seg;
     const uint32_t nd = min(ctl->ndeep, job->cap_deep);
-    const uint32_t kk = ctl->deep_kk, jj = ctl->deep_jj;
+    if (nd == 0u) return;
+    deep_tiles_body<KIND>(job, nd, reinterpret_cast<C *>(deep_raw), s_seg);
+}
+
+// The stage after (merge width 2^kk, stride 2^jj): the global half-cleaners down to
+// stride 2^12, then the on-chip strides, then the next merge's mirror stage.
+__device__ __forceinline__ void deep_next(uint32_t &kk, uint32_t &jj) {
+    if (jj > 12u) jj--;
+    else if (jj == 12u) jj = 11u;
+    else { kk++; jj = kk - 1u; }
+}
+
+// One stage for every deep segment whose padded length reaches the merge width 2^kk.
+template <int KIND>
+__device__ __forceinline__ void deep_stage_body(const Job *__restrict__ job, uint32_t nd, uint32_t kk,
+                                                uint32_t jj, typename Key<KIND>::C *sm, uint32_t &s_seg) {
+    using K = Key<KIND>;
+    using S = typename K::S;
     if (jj >= 12u) {                                      // a global stride
         const uint32_t total = job->deep_chunks[nd];
         const bool mirror = jj == kk - 1u;
@@ -2029,14 +2041,25 @@ __global__ void __launch_bounds__(kDeepThreads) k_deep_stage(const Job *__restri
             deep_tile<KIND>(job, it, t - job->deep_tiles[s], sm, false);
         }
     }
+}
+
+// One stage per launch; the last block to finish advances the stage and sets the loop
+// condition.
+template <int KIND>
+__global__ void __launch_bounds__(kDeepThreads) k_deep_stage(const Job *__restrict__ job, Ctl *ctl,
+                                                             cudaGraphConditionalHandle h, int use_handle) {
+    using C = typename Key<KIND>::C;
+    extern __shared__ __align__(16) unsigned char deep_raw[];
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    const uint32_t kk = ctl->deep_kk, jj = ctl->deep_jj;
+    deep_stage_body<KIND>(job, nd, kk, jj, reinterpret_cast<C *>(deep_raw), s_seg);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(&ctl->deep_blocks, 1u) + 1u == gridDim.x) {
             uint32_t nk = kk, nj = jj;
-            if (nj > 12u) nj--;                           // next global half-cleaner
-            else if (nj == 12u) nj = 11u;                 // then the on-chip strides
-            else { nk++; nj = nk - 1u; }                  // then the next merge's mirror
+            deep_next(nk, nj);
             const uint32_t cont = (nk <= ctl->deep_maxlog && ctl->status == 0u) ? 1u : 0u;
             ctl->deep_kk = nk;
             ctl->deep_jj = nj;
@@ -2049,12 +2072,10 @@ __global__ void __launch_bounds__(kDeepThreads) k_deep_stage(const Job *__restri
 
 // Moves every deep segment to the output array when its buffer is not the output.
 template <int KIND>
-__global__ void k_deep_finish(const Job *__restrict__ job, Ctl *ctl) {
+__device__ __forceinline__ void deep_finish_body(const Job *__restrict__ job, Ctl *ctl, uint32_t nd,
+                                                 uint32_t &s_seg) {
     using K = Key<KIND>;
     using S = typename K::S;
-    __shared__ uint32_t s_seg;
-    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
-    if (nd == 0u) return;
     const uint32_t total = job->deep_tiles[nd];
     S *out = reinterpret_cast<S *>(job->out);
     for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -2072,6 +2093,71 @@ __global__ void k_deep_finish(const Job *__restrict__ job, Ctl *ctl) {
         const uint64_t end = min(base + (uint64_t)kDeepTile, (uint64_t)it.begin + it.len);
         for (uint64_t i = base + threadIdx.x; i < end; i += blockDim.x) out[i] = buf[i];
     }
+}
+
+template <int KIND>
+__global__ void k_deep_finish(const Job *__restrict__ job, Ctl *ctl) {
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(ctl->ndeep, job->cap_deep);
+    if (nd == 0u) return;
+    deep_finish_body<KIND>(job, ctl, nd, s_seg);
+}
+
+// Barrier over the whole grid of a cooperative launch (every block resident).  The last
+// block to arrive publishes, with the next generation, whether the status is still clean,
+// so every block takes the same decision; a wait that runs past `limit` polls sets
+// TSQS_ETIMEOUT.  False: stop (the status is set).
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t &gen, uint32_t limit) {
+    __shared__ uint32_t s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        uint32_t go = 0u;
+        if (atomicAdd(&ctl->coop_count, 1u) + 1u == gridDim.x) {
+            ctl->coop_count = 0u;
+            ctl->coop_go = *(volatile const uint32_t *)&ctl->status == 0u ? 1u : 0u;
+            __threadfence();
+            atomicExch(&ctl->coop_gen, gen + 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*(volatile const uint32_t *)&ctl->coop_gen == gen) {
+                if (++polls >= limit) { set_status(ctl, TSQS_ETIMEOUT); break; }
+                __nanosleep(polls < 64 ? 32 : 256);
+            }
+            __threadfence();
+        }
+        go = *(volatile const uint32_t *)&ctl->coop_gen == gen + 1u ? *(volatile const uint32_t *)&ctl->coop_go : 0u;
+        s_go = go;
+    }
+    __syncthreads();
+    gen++;
+    return s_go != 0u;
+}
+
+// The depth guard's whole branch in one cooperative launch (the task schedule's graph
+// holds no conditional node): prep, tile sorts, every stage, finish, with a grid barrier
+// between steps.  With no deep segment every block returns at once.
+template <int KIND>
+__global__ void __launch_bounds__(kDeepThreads) k_deep_all(const Job *__restrict__ job, Ctl *ctl) {
+    using C = typename Key<KIND>::C;
+    extern __shared__ __align__(16) unsigned char deep_raw[];
+    C *sm = reinterpret_cast<C *>(deep_raw);
+    __shared__ uint32_t s_seg;
+    const uint32_t nd = min(*(volatile const uint32_t *)&ctl->ndeep, job->cap_deep);
+    if (nd == 0u || *(volatile const uint32_t *)&ctl->status != 0u) return;
+    const uint32_t limit = job->spin_limit;
+    uint32_t gen = 0;
+    if (blockIdx.x == 0) deep_prep_body(job, ctl);
+    if (!grid_barrier(ctl, gen, limit)) return;
+    deep_tiles_body<KIND>(job, nd, sm, s_seg);
+    if (!grid_barrier(ctl, gen, limit)) return;
+    const uint32_t maxlog = *(volatile const uint32_t *)&ctl->deep_maxlog;
+    for (uint32_t kk = 13u, jj = 12u; kk <= maxlog;) {
+        deep_stage_body<KIND>(job, nd, kk, jj, sm, s_seg);
+        if (!grid_barrier(ctl, gen, limit)) return;
+        deep_next(kk, jj);
+    }
+    deep_finish_body<KIND>(job, ctl, nd, s_seg);
 }
 
 // Level control (one thread).  Records the level's statistics, resets the consumed
