@@ -2146,7 +2146,8 @@ __global__ void __launch_bounds__(kDeepThreads) k_deep_all(const Job *__restrict
     const uint32_t nd = min(*(volatile const uint32_t *)&ctl->ndeep, job->cap_deep);
     if (nd == 0u || *(volatile const uint32_t *)&ctl->status != 0u) return;
     const uint32_t limit = job->spin_limit;
-    uint32_t gen = 0;
+    // the barrier's generation goes on from any earlier cooperative launch of this call
+    uint32_t gen = *(volatile const uint32_t *)&ctl->coop_gen;
     if (blockIdx.x == 0) deep_prep_body(job, ctl);
     if (!grid_barrier(ctl, gen, limit)) return;
     deep_tiles_body<KIND>(job, nd, sm, s_seg);
