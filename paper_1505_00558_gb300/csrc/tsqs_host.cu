@@ -599,14 +599,11 @@ int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     kp.func = (void *)o->k_task_init;
     kp.gridDim = dim3(c->sms * 2);
     CK(cudaGraphAddKernelNode(&n_init, g, &n_pre, 1, &kp));
-    cudaGraphConditionalHandle h_none = 0;
-    int use_h = 0;
-    void *argst[] = {&pj, &pc, &h_none, &use_h};
     kp = cudaKernelNodeParams{};
     kp.func = (void *)o->k_task;
     kp.gridDim = dim3(c->task_grid[o->kind]);
     kp.blockDim = dim3(o->task_block);
-    kp.kernelParams = argst;
+    kp.kernelParams = args2;
     CK(cudaGraphAddKernelNode(&n_task, g, &n_init, 1, &kp));
     int leaf_last = 1;
     void *argsl[] = {&pj, &pc, &leaf_last};
@@ -1257,10 +1254,9 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
     CK(cudaLaunchKernel(o->k_presort, dim3(c->sms * 4), dim3(256), args2, 0, s));
     if (task) {
         // task schedule: init, the task kernel, the leaf pass, the depth guard if needed
-        void *argst[] = {&pj, &pc, &h, &use_h};
         CK(cudaLaunchKernel(o->k_task_init, dim3(c->sms * 2), dim3(256), args2, 0, s));
         CK(cudaEventRecord(ev[0], s));
-        CK(cudaLaunchKernel(o->k_task, dim3(c->task_grid[k]), dim3(o->task_block), argst, 0, s));
+        CK(cudaLaunchKernel(o->k_task, dim3(c->task_grid[k]), dim3(o->task_block), args2, 0, s));
         CK(cudaEventRecord(ev[1], s));
         CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl_last,
                             (size_t)o->leaf_smem, s));

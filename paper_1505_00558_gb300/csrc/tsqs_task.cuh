@@ -218,12 +218,10 @@ __global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
     }
 }
 
-// The task kernel (persistent; BLOCK threads, tiles of BLOCK x ITEMS keys).  When the
-// last segment finishes, the block that finished it sets the depth guard's branch
-// (graph launches: use_handle) from the deep queue.
+// The task kernel (persistent; BLOCK threads, tiles of BLOCK x ITEMS keys).  Segments
+// handed to the depth guard wait in its queue for the cooperative kernel that follows.
 template <int KIND, int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restrict__ job, Ctl *ctl,
-                                                cudaGraphConditionalHandle h_deep, int use_handle) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
@@ -488,11 +486,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
             const uint32_t ta = s_ta;
             for (uint32_t g = (uint32_t)tid; g < active && (uint64_t)ta + g < job->cap_trow; g += BLOCK)
                 st_relaxed(job->trow + ta + g, kTaskEndRow);
-            if (tid == 0 && use_handle) {
-                __threadfence();
-                const bool ok = *(volatile const uint32_t *)&ctl->status == 0u;
-                cudaGraphSetConditional(h_deep, (ok && *(volatile const uint32_t *)&ctl->ndeep != 0u) ? 1u : 0u);
-            }
         }
     }
 }
