@@ -19,7 +19,8 @@
 //     leaf queue (<= small_T, Section IV's role), to the depth guard's queue, or as new
 //     segments partitioned as soon as their blocks pick them up;
 //   - a count of live segments falling to zero ends the launch: the block that sees it
-//     writes end-of-work rows for every block still polling.
+//     writes end-of-work rows for every block still polling (a launch that starts with
+//     none ends at once).
 // Keys of depth d are in buffer d % 2, as level d's are in the level-synchronous loop,
 // and the output of every step (leaf items, fills, deep items) is the same.
 #pragma once
@@ -174,12 +175,10 @@ __device__ __forceinline__ void push_leaf(const Job *job, Ctl *ctl, uint64_t b, 
 }
 
 // Seeds the task schedule: one warp per root segment (grid-stride).  Roots above the
-// on-chip threshold become task segments of depth 0, smaller ones leaf items; the last
-// block writes end-of-work rows if no task was pushed.
+// on-chip threshold become task segments of depth 0, smaller ones leaf items.
 template <int KIND>
 __global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
     using K = Key<KIND>;
-    __shared__ uint32_t s_last;
     const uint64_t nseg = job->seg_offsets ? job->nseg : 1;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
@@ -201,21 +200,6 @@ __global__ void k_task_init(const Job *__restrict__ job, Ctl *ctl) {
         }
     }
     if (lane == 0 && pushed) atomicAdd(&ctl->live, pushed);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&ctl->blocks_done, 1u) + 1u == gridDim.x ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        if (*(volatile const uint32_t *)&ctl->live == 0u) {
-            const uint32_t ta = *(volatile const uint32_t *)&ctl->talloc;
-            for (uint32_t g = threadIdx.x; g < job->task_grid && (uint64_t)ta + g < job->cap_trow; g += blockDim.x)
-                st_relaxed(job->trow + ta + g, kTaskEndRow);
-        }
-        if (threadIdx.x == 0) ctl->blocks_done = 0u;
-    }
 }
 
 // The task kernel (persistent; BLOCK threads, tiles of BLOCK x ITEMS keys).  Segments
@@ -243,6 +227,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
     const int64_t e_hi = n - ((n + (int64_t)vec_off) % V);
     const uint64_t T = job->small_T;
     const uint32_t spin_limit = job->spin_limit;
+    // no task segment (every root was small, in order or empty): nothing to wait for
+    if (*(volatile const uint32_t *)&ctl->live == 0u) return;
     // blocks past the ones this input can use leave at once (their SMs go to other work)
     const uint32_t active = min(gridDim.x, job->task_grid);
     if (blockIdx.x >= active) return;
