@@ -46,8 +46,8 @@ struct alignas(16) TaskSeg {
     uint64_t piv_lo, piv_hi;  // canonical pivot
     uint32_t tile_begin;      // first global tile id (tile ids run over the whole sort)
     uint32_t ntiles_depth;    // tiles | recursion depth << 24 (keys in buffer depth % 2)
-    unsigned long long done;  // finished tiles << 44 | their #<p << 22 | their #>p (the
-                              // counts only for segments below 2^22 elements)
+    unsigned long long done;  // finished tiles << 42 | their #<p << 21 | their #>p (the
+                              // counts only for segments below 2^21 elements)
     unsigned long long cursor;   // reserved (#<p | #>p << 32)
 };
 static_assert(sizeof(TaskSeg) == 64, "TaskSeg is four 16-byte words");

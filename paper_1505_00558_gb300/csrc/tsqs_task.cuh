@@ -70,9 +70,10 @@ __device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long lon
     return old;
 }
 
-// Finished-tile word: the tile count above bit 44; below 2^22 elements a segment's tiles
-// also add their (#<p, #>p), so the last one reads the totals from its own atomic.
-constexpr int kDoneTiles = 44, kDoneCount = 22;
+// Finished-tile word: the tile count above bit 42 (2^22 tiles cover a segment of 2^31
+// records in tiles of 1024); below 2^21 elements a segment's tiles also add their
+// (#<p, #>p) in two 21-bit fields, so the last one reads the totals from its own atomic.
+constexpr int kDoneTiles = 42, kDoneCount = 21;
 constexpr uint64_t kDoneSmall = 1ull << kDoneCount;
 constexpr unsigned long long kDoneMask = (1ull << kDoneCount) - 1ull;
 
@@ -124,7 +125,7 @@ __device__ bool push_task(const Job *job, Ctl *ctl, uint64_t b, uint64_t e, uint
     const typename K::C p = sample_pivot<K, true>(buffer<K>(job, (int)(d & 1u)), b, e,
                                                   job->samples, job->seed, nullptr);
     if (lane == 0) {
-        ok = (fi < job->cap_tseg && fi < 0x80000000u && nt < (1u << 20) && d < 256u &&
+        ok = (fi < job->cap_tseg && fi < 0x80000000u && nt < (1u << 22) && d < 256u &&
               (uint64_t)tb + nt + kTaskGridMax <= job->cap_trow) ? 1u : 0u;
         if (ok) {
             TaskSeg ts;
