@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="one instrumented (host-driven, one launch per kernel) sort of the "
                          "uniform workload and nothing else: the case the ncu captures use")
-    ap.add_argument("--kind", default="i32", choices=["i32", "i64", "rec"],
-                    help="with --profile: int32, int64 (uniform 64-bit) or {u64, u64} records")
+    ap.add_argument("--kind", default="i32", choices=["i32", "i64", "f32", "rec"],
+                    help="with --profile: int32, int64 (uniform 64-bit), float32 (~N(0,1) with "
+                         "specials) or {u64, u64} records")
     return ap.parse_args()
 
 
@@ -350,6 +351,10 @@ def profile_case(args, dist):
     elif args.kind == "i64":
         kind, label = T.TSQS_I64, "int64 uniform random"
         src = torch.from_numpy(rand_u64(1, 64, n).view(np.int64)).cuda()
+    elif args.kind == "f32":
+        from workloads import floats_normal_specials
+        kind, label = T.TSQS_F32, "float32 ~N(0,1) with specials (raw bits)"
+        src = torch.from_numpy(floats_normal_specials(n, seed=1).view(np.int32).copy()).cuda()
     else:
         kind, label = T.TSQS_I32, "int32 uniform random"
         src = torch.from_numpy(int32_pattern("random", n, seed=1)).cuda()
@@ -364,6 +369,10 @@ def profile_case(args, dist):
         flip = torch.tensor(-(1 << 63), dtype=torch.int64, device=src.device)
         k, p = src[:, 0] ^ flip, src[:, 1] ^ flip
         ok = ctx.status() == 0 and bool(((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (p[1:] >= p[:-1]))).all().item())
+    elif kind == T.TSQS_F32:
+        # IEEE totalOrder on the raw bits: negative values flip their low 31 bits
+        k = src ^ ((src >> 31) & 0x7FFFFFFF)
+        ok = ctx.status() == 0 and bool((k[1:] >= k[:-1]).all().item())
     else:
         ok = ctx.status() == 0 and bool((src[1:] >= src[:-1]).all().item())
     if dist.rank == 0:

@@ -103,6 +103,19 @@ template <> struct Key<TSQS_U64_U64_REC> {
     static __device__ __forceinline__ D pdom(C c) { return c; }
 };
 
+// Comparison against a pivot fixed for a whole tile.  RawDom compares the storage words
+// as integers of type T; CanonDom through the key kind's own domain.  Float keys use
+// raw words (float_raw_classify): with a pivot whose sign bit is clear, a signed compare
+// of the raw words is IEEE totalOrder; with it set, an unsigned compare is the reverse
+// order, so the <p and >p masks swap.  That saves the per-key canonical transform.
+template <class T> struct RawDom {
+    template <class S> __device__ __forceinline__ T operator()(S x) const { return (T)x; }
+};
+template <class K> struct CanonDom {
+    __device__ __forceinline__ typename K::D operator()(typename K::S x) const { return K::dom(x); }
+};
+template <int KIND> constexpr bool kFloatKind = KIND == TSQS_F32 || KIND == TSQS_F64;
+
 // canonical-order helpers, overloaded on C (and on the comparison domains D)
 __device__ __forceinline__ bool c_lt(int a, int b) { return a < b; }
 __device__ __forceinline__ bool c_lt(long long a, long long b) { return a < b; }
@@ -924,18 +937,18 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
         S v[ITEMS];
         uint32_t ltm = 0, gtm = 0;
         if (work) {
-            const D pd = K::pdom(c_from<C>(m.piv_lo, m.piv_hi));
             const int64_t sb = (int64_t)m.sb, se = (int64_t)m.se;
             const bool full_tile = m.t0 >= sb && m.t0 + TILE <= se && m.cs == m.t0 && m.ce == m.t0 + TILE;
             // tile-local bounds of the segment and of the bulk-copied range
             const int lo = (int)max((int64_t)0, sb - m.t0), hi = (int)min((int64_t)TILE, se - m.t0);
             const bool covered = m.cs - m.t0 <= lo && m.ce - m.t0 >= hi;
+            auto classify = [&](auto dom, auto pd) {
             if (full_tile) {                             // interior tile: no bounds checks
 #pragma unroll
                 for (int k = 0; k < NV; k++) lds_vec<S, V>(buf + (k * BLOCK + tid) * V, &v[k * V]);
 #pragma unroll
                 for (int i = 0; i < ITEMS; i++) {
-                    const D d = K::dom(v[i]);
+                    const auto d = dom(v[i]);
                     if (c_lt(d, pd)) ltm |= 1u << i;
                     if (c_lt(pd, d)) gtm |= 1u << i;
                 }
@@ -952,7 +965,7 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
                     if (vs >= lo && vs + V <= hi) {
 #pragma unroll
                         for (int j = 0; j < V; j++) {
-                            const D d = K::dom(v[k * V + j]);
+                            const auto d = dom(v[k * V + j]);
                             if (c_lt(d, pd)) ltm |= 1u << (k * V + j);
                             if (c_lt(pd, d)) gtm |= 1u << (k * V + j);
                         }
@@ -960,7 +973,7 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
 #pragma unroll
                         for (int j = 0; j < V; j++) {
                             const bool in = vs + j >= lo && vs + j < hi;
-                            const D d = K::dom(v[k * V + j]);
+                            const auto d = dom(v[k * V + j]);
                             ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
                             gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
                         }
@@ -975,12 +988,27 @@ __global__ void __launch_bounds__(BLOCK + 32, part_min_blocks(BLOCK, ITEMS * (in
                         const int64_t e = m.t0 + idx;
                         if (e >= sb && e < se) {
                             v[k * V + j] = (e >= m.cs && e < m.ce) ? buf[idx] : src[e];
-                            const D d = K::dom(v[k * V + j]);
+                            const auto d = dom(v[k * V + j]);
                             ltm |= (uint32_t)c_lt(d, pd) << (k * V + j);
                             gtm |= (uint32_t)c_lt(pd, d) << (k * V + j);
                         }
                     }
                 }
+            }
+            };
+            if constexpr (kFloatKind<KIND>) {
+                using SI = typename std::make_signed<S>::type;
+                const S praw = K::uncanon(c_from<C>(m.piv_lo, m.piv_hi));
+                if ((SI)praw >= 0) {
+                    classify(RawDom<SI>{}, (SI)praw);
+                } else {
+                    classify(RawDom<S>{}, praw);
+                    const uint32_t t = ltm;
+                    ltm = gtm;
+                    gtm = t;
+                }
+            } else {
+                classify(CanonDom<K>{}, K::pdom(c_from<C>(m.piv_lo, m.piv_hi)));
             }
         }
         const uint32_t cnt = (uint32_t)__popc(ltm) | ((uint32_t)__popc(gtm) << 16);

@@ -210,7 +210,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
     using K = Key<KIND>;
     using S = typename K::S;
     using C = typename K::C;
-    using D = typename K::D;
     constexpr int TILE = BLOCK * ITEMS, V = K::V, NV = ITEMS / V, NW = BLOCK / 32;
     static_assert(ITEMS % V == 0 && ITEMS <= 32 && TILE < 65536 && NW >= 4, "tile shape");
     __shared__ __align__(16) S buf[TILE + V];      // staged runs + one dummy 16-byte slot
@@ -300,12 +299,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
         // block places its runs at the segment's ends and finishes it
         const bool single = ntiles == 1u;
         const C pc = c_from<C>(s_seg.piv_lo, s_seg.piv_hi);
-        const D pd = K::pdom(pc);
         uint32_t ltm = 0, gtm = 0;
+        auto classify = [&](auto dom, auto pd) {
         if (t0 >= sb && t0 + TILE <= se) {
 #pragma unroll
             for (int i = 0; i < ITEMS; i++) {
-                const D d = K::dom(v[i]);
+                const auto d = dom(v[i]);
                 if (c_lt(d, pd)) ltm |= 1u << i;
                 if (c_lt(pd, d)) gtm |= 1u << i;
             }
@@ -316,11 +315,28 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_task(const Job *__restr
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     const bool in = vs + j >= sb && vs + j < se;
-                    const D d = K::dom(v[k * V + j]);
+                    const auto d = dom(v[k * V + j]);
                     ltm |= (uint32_t)(in && c_lt(d, pd)) << (k * V + j);
                     gtm |= (uint32_t)(in && c_lt(pd, d)) << (k * V + j);
                 }
             }
+        }
+        };
+        if constexpr (kFloatKind<KIND>) {
+            // raw words against the pivot's sign (see RawDom): signed compare, or unsigned
+            // compare with the masks swapped
+            using SI = typename std::make_signed<S>::type;
+            const S praw = K::uncanon(pc);
+            if ((SI)praw >= 0) {
+                classify(RawDom<SI>{}, (SI)praw);
+            } else {
+                classify(RawDom<S>{}, praw);
+                const uint32_t t = ltm;
+                ltm = gtm;
+                gtm = t;
+            }
+        } else {
+            classify(CanonDom<K>{}, K::pdom(pc));
         }
 
         // ---- block offsets, reservation on the segment's cursor, staging
