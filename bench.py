@@ -44,8 +44,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-width k_partition launch at the
 # headline size (2^27 int32, level 3 of an instrumented sort): 537.1 MB + 479.1 MB for
 # 134,217,721 keys; valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"kernels_sha": "6b464edbb912038a",
-               "bytes_per_key": (537056256 + 478899712) / 134217721,
+NCU_TRAFFIC = {"kernels_sha": "c914553cd5b4a838",
+               "bytes_per_key": (537056000 + 479370240) / 134217721,
                "source": "profiles/k_partition_2e27_int32_traffic.md"}
 
 
