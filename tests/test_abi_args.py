@@ -112,3 +112,27 @@ def test_plan_defaults_and_scratch_bounds(T):
         b = L.tsqs_scratch_bytes_for(1 << 22, 1, es, ctypes.byref(plan))
         c = L.tsqs_scratch_bytes_for(1 << 22, 5000, es, ctypes.byref(plan))
         assert (1 << 20) * es < a < b <= c        # at least the second buffer, growing with n and nseg
+
+
+def test_schedule_decides_the_task_tables(T):
+    """The task-parallel schedule's tables are part of the scratch exactly when a sort of
+    that size takes it: below the 2^24 bound by default (schedule 0), at any size with
+    schedule 2, never with schedule 1 or look-back offsets (no GPU needed)."""
+    L = T.lib()
+
+    def need(n, schedule, offset_mode=0):
+        p = T.Plan()
+        assert L.tsqs_plan_default(T.TSQS_I32, 0, ctypes.byref(p)) == T.TSQS_OK
+        p.schedule = schedule
+        p.offset_mode = offset_mode
+        return L.tsqs_scratch_bytes_for(n, 1, 4, ctypes.byref(p))
+
+    for n in (1 << 16, 1_000_000, 1 << 24):
+        assert need(n, 0) > need(n, 1)            # task tables below the bound
+        assert need(n, 0) == need(n, 2)
+        assert need(n, 0, offset_mode=1) == need(n, 1)
+    for n in ((1 << 24) + 1, 1 << 26):
+        assert need(n, 0) == need(n, 1)           # level by level above it
+        assert need(n, 2) > need(n, 1)
+    # the tables stay a small fraction of the second buffer
+    assert need(1 << 24, 0) - need(1 << 24, 1) < (1 << 24) * 4
