@@ -209,7 +209,7 @@ int tsqs_ctx_sort_segmented(tsqs_ctx *ctx, void *base, size_t nmemb_total,
  *                        schedule of the ctx's plan (tsqs_plan.schedule: task-parallel up
  *                        to 2^24 elements by default, level by level above) releases that
  *                        graph, builds the other one and stores its new handle in
- *                        *graph_exec.
+ *                        *graph_exec; within one schedule the handle stays.
  * The graph holds the same nodes as the ctx's own sort for that size: presortedness, then
  * the task kernel or the conditional level loop, the leaf pass and the depth guard.
  * d_seg_offsets == NULL sorts base[0, nmemb_total) as one segment; otherwise as

@@ -80,6 +80,11 @@ bool task_schedule(const tsqs_plan &p, size_t n) {
     return p.schedule == 2 || n <= kTaskMaxN;
 }
 
+// Up to this many elements the task graph's leaf pass takes the small-input leaf kernel:
+// its items fit in one wave, and more threads per item shorten the pass (1e6 int32:
+// 7.5 us); above it the default leaf's throughput wins.
+constexpr size_t kSmallLeafN = size_t(1) << 20;
+
 struct Layout {
     size_t alt_off, front_off[2], leaves_off, tseg_off, tstat_off, done_off, cursor_off, presort_off,
         deep_off, dtiles_off, dchunks_off, misc_off, ttask_off, trow_off, total;
@@ -192,9 +197,11 @@ struct tsqs_ctx {
     size_t scratch_bytes = 0;
     cudaGraph_t graph[8] = {};
     cudaGraphExec_t exec[8] = {};
-    cudaGraph_t graph_task[8] = {};      // the task-parallel schedule's graph per kind
-    cudaGraphExec_t exec_task[8] = {};
-    int part_grid[8] = {}, leaf_grid[8] = {}, task_grid[8] = {}, deep_grid[8] = {};
+    // the task-parallel schedule's graphs per kind: [0] with the leaf pass of k_leaf,
+    // [1] with k_leaf_small (small inputs)
+    cudaGraph_t graph_task[8][2] = {};
+    cudaGraphExec_t exec_task[8][2] = {};
+    int part_grid[8] = {}, leaf_grid[8] = {}, leaf_small_grid[8] = {}, task_grid[8] = {}, deep_grid[8] = {};
     bool attrs_set[8] = {};
     cudaEvent_t done_ev = nullptr;
     bool ev_valid = false;
@@ -212,7 +219,8 @@ struct tsqs_ctx {
     size_t item_status_cap = 0;
     // caller-held graphs (tsqs_graph_sort_segmented): each exec with its graph, the
     // setup node whose Job argument a later call updates, and its key kind
-    struct Held { cudaGraphExec_t exec; cudaGraph_t graph; cudaGraphNode_t setup; int kind; bool task; };
+    // variant: 0 level by level, 1 task-parallel, 2 task-parallel with the small-input leaf
+    struct Held { cudaGraphExec_t exec; cudaGraph_t graph; cudaGraphNode_t setup; int kind; int variant; };
     std::vector<Held> held;
     std::recursive_mutex mu;
 };
@@ -247,6 +255,7 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     const int k = o->kind;
     if (c->attrs_set[k]) return TSQS_OK;
     CK(cudaFuncSetAttribute(o->k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_smem));
+    CK(cudaFuncSetAttribute(o->k_leaf_small, cudaFuncAttributeMaxDynamicSharedMemorySize, o->leaf_small_smem));
     CK(cudaFuncSetAttribute(o->k_deep_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem));
     CK(cudaFuncSetAttribute(o->k_deep_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem));
     CK(cudaFuncSetAttribute(o->k_deep_all, cudaFuncAttributeMaxDynamicSharedMemorySize, o->deep_smem));
@@ -257,6 +266,10 @@ int ctx_kind_setup(tsqs_ctx *c, const KindOps *o) {
     int occ_p = 0, occ_l = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pv.k_partition, pv.threads, pv.smem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, o->k_leaf, o->leaf_block, o->leaf_smem));
+    int occ_ls = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ls, o->k_leaf_small, o->leaf_small_block,
+                                                     o->leaf_small_smem));
+    c->leaf_small_grid[k] = std::max(1, occ_ls) * c->sms;
     int occ_t = 0, occ_d = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, o->k_task, o->task_block, 0));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, o->k_deep_all, 512, o->deep_smem));
@@ -579,7 +592,8 @@ int ctx_build_graph(tsqs_ctx *c, const KindOps *o) {
 // The task schedule's graph for kind o:
 //     orient -> check -> presort -> task init -> task kernel -> leaf pass -> depth guard
 // with the depth guard as one cooperative kernel (no conditional node).
-int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep = nullptr) {
+int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGraphNode_t *dep,
+                     bool small_leaf) {
     Job *pj = c->d_job;
     Ctl *pc = c->d_ctl;
     void *args2[] = {&pj, &pc};
@@ -608,10 +622,10 @@ int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     int leaf_last = 1;
     void *argsl[] = {&pj, &pc, &leaf_last};
     kp = cudaKernelNodeParams{};
-    kp.func = (void *)o->k_leaf;
-    kp.gridDim = dim3(c->leaf_grid[o->kind]);
-    kp.blockDim = dim3(o->leaf_block);
-    kp.sharedMemBytes = (unsigned)o->leaf_smem;
+    kp.func = small_leaf ? (void *)o->k_leaf_small : (void *)o->k_leaf;
+    kp.gridDim = dim3(small_leaf ? c->leaf_small_grid[o->kind] : c->leaf_grid[o->kind]);
+    kp.blockDim = dim3(small_leaf ? o->leaf_small_block : o->leaf_block);
+    kp.sharedMemBytes = (unsigned)(small_leaf ? o->leaf_small_smem : o->leaf_smem);
     kp.kernelParams = argsl;
     CK(cudaGraphAddKernelNode(&n_leaf, g, &n_task, 1, &kp));
     // the depth guard as one cooperative kernel, which returns at once when no segment
@@ -631,12 +645,12 @@ int build_task_nodes(tsqs_ctx *c, const KindOps *o, cudaGraph_t g, const cudaGra
     return TSQS_OK;
 }
 
-int ctx_build_task_graph(tsqs_ctx *c, const KindOps *o) {
+int ctx_build_task_graph(tsqs_ctx *c, const KindOps *o, int v) {
     const int k = o->kind;
-    if (c->exec_task[k]) return TSQS_OK;
+    if (c->exec_task[k][v]) return TSQS_OK;
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
-    int rc = build_task_nodes(c, o, g);
+    int rc = build_task_nodes(c, o, g, nullptr, v == 1);
     cudaGraphExec_t ex = nullptr;
     if (rc == TSQS_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) rc = TSQS_ECUDA;
     if (rc) {
@@ -644,8 +658,8 @@ int ctx_build_task_graph(tsqs_ctx *c, const KindOps *o) {
         cudaGraphDestroy(g);
         return rc;
     }
-    c->graph_task[k] = g;
-    c->exec_task[k] = ex;
+    c->graph_task[k][v] = g;
+    c->exec_task[k][v] = ex;
     return TSQS_OK;
 }
 
@@ -691,14 +705,15 @@ int ctx_launch(tsqs_ctx *c, void *base, size_t n, const uint64_t *offs, size_t n
     if ((rc = ctx_kind_setup(c, o))) return rc;
     if ((rc = ctx_ensure_scratch(c, o, n, offs ? nseg : 1))) return rc;
     const bool task = task_schedule(c->plan, n);
-    if ((rc = task ? ctx_build_task_graph(c, o) : ctx_build_graph(c, o))) return rc;
+    const int tv = (task && n <= kSmallLeafN) ? 1 : 0;       // task graph variant
+    if ((rc = task ? ctx_build_task_graph(c, o, tv) : ctx_build_graph(c, o))) return rc;
     Job j;
     if ((rc = make_job(c, o, base, n, offs, nseg, &j, task))) return rc;
     if (out) j.out = out;
     if (c->ev_valid) CK(cudaStreamWaitEvent(stream, c->done_ev, 0));
     k_setup<<<1, 256, 0, stream>>>(c->d_job, c->d_ctl, j);
     CK(cudaGetLastError());
-    CK(cudaGraphLaunch(task ? c->exec_task[key_kind] : c->exec[key_kind], stream));
+    CK(cudaGraphLaunch(task ? c->exec_task[key_kind][tv] : c->exec[key_kind], stream));
     CK(cudaEventRecord(c->done_ev, stream));
     c->ev_valid = true;
     return TSQS_OK;
@@ -792,8 +807,10 @@ void tsqs_ctx_destroy(tsqs_ctx *c) {
         for (int k = 0; k < 8; k++) {
             if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
             if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
-            if (c->exec_task[k]) cudaGraphExecDestroy(c->exec_task[k]);
-            if (c->graph_task[k]) cudaGraphDestroy(c->graph_task[k]);
+            for (int v = 0; v < 2; v++) {
+                if (c->exec_task[k][v]) cudaGraphExecDestroy(c->exec_task[k][v]);
+                if (c->graph_task[k][v]) cudaGraphDestroy(c->graph_task[k][v]);
+            }
         }
         for (auto &h : c->held) {
             cudaGraphExecDestroy(h.exec);
@@ -831,12 +848,14 @@ int tsqs_ctx_set_plan(tsqs_ctx *c, const tsqs_plan *plan) {
     for (int k = 0; k < 8; k++) {            // grids depend on the plan
         if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
         if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
-        if (c->exec_task[k]) cudaGraphExecDestroy(c->exec_task[k]);
-        if (c->graph_task[k]) cudaGraphDestroy(c->graph_task[k]);
+        for (int v = 0; v < 2; v++) {
+            if (c->exec_task[k][v]) cudaGraphExecDestroy(c->exec_task[k][v]);
+            if (c->graph_task[k][v]) cudaGraphDestroy(c->graph_task[k][v]);
+            c->exec_task[k][v] = nullptr;
+            c->graph_task[k][v] = nullptr;
+        }
         c->exec[k] = nullptr;
         c->graph[k] = nullptr;
-        c->exec_task[k] = nullptr;
-        c->graph_task[k] = nullptr;
         c->attrs_set[k] = false;
     }
     return TSQS_OK;
@@ -885,6 +904,7 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     if ((rc = ctx_kind_setup(c, o))) return rc;
     if ((rc = ctx_ensure_scratch(c, o, nmemb_total, offs ? nseg : 1))) return rc;
     const bool task = task_schedule(c->plan, nmemb_total);
+    const int variant = task ? (nmemb_total <= kSmallLeafN ? 2 : 1) : 0;
     Job j;
     if ((rc = make_job(c, o, base, nmemb_total, offs, offs ? nseg : 1, &j, task))) return rc;
     Job *pj = c->d_job;
@@ -895,8 +915,9 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(256);
     kp.kernelParams = args;
-    if (h && h->task != task) {
-        // this size takes the other schedule: the graph is rebuilt under a new handle
+    if (h && (h->variant == 0) != (variant == 0)) {
+        // this size takes the other schedule: the graph is rebuilt under a new handle (a
+        // task graph keeps the leaf kernel it was built with: either sorts every item)
         ctx_quiesce(c);
         cudaGraphExecDestroy(h->exec);
         cudaGraphDestroy(h->graph);
@@ -907,10 +928,11 @@ int tsqs_graph_sort_segmented(tsqs_ctx *c, void *base, size_t nmemb_total,
     if (!h) {
         tsqs_ctx::Held nh{};
         nh.kind = key_kind;
-        nh.task = task;
+        nh.variant = variant;
         CK(cudaGraphCreate(&nh.graph, 0));
         rc = cudaGraphAddKernelNode(&nh.setup, nh.graph, nullptr, 0, &kp) == cudaSuccess
-                 ? (task ? build_task_nodes(c, o, nh.graph, &nh.setup) : build_sort_nodes(c, o, nh.graph, &nh.setup))
+                 ? (task ? build_task_nodes(c, o, nh.graph, &nh.setup, variant == 2)
+                         : build_sort_nodes(c, o, nh.graph, &nh.setup))
                  : TSQS_ECUDA;
         if (rc == TSQS_OK && cudaGraphInstantiate(&nh.exec, nh.graph, 0) != cudaSuccess) rc = TSQS_ECUDA;
         if (rc) {
@@ -1258,8 +1280,12 @@ int tsqs_ctx_sort_timed(tsqs_ctx *c, void *base, size_t nmemb, size_t elem_size,
         CK(cudaEventRecord(ev[0], s));
         CK(cudaLaunchKernel(o->k_task, dim3(c->task_grid[k]), dim3(o->task_block), args2, 0, s));
         CK(cudaEventRecord(ev[1], s));
-        CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl_last,
-                            (size_t)o->leaf_smem, s));
+        if (nmemb <= kSmallLeafN)
+            CK(cudaLaunchKernel(o->k_leaf_small, dim3(c->leaf_small_grid[k]), dim3(o->leaf_small_block),
+                                argsl_last, (size_t)o->leaf_small_smem, s));
+        else
+            CK(cudaLaunchKernel(o->k_leaf, dim3(c->leaf_grid[k]), dim3(o->leaf_block), argsl_last,
+                                (size_t)o->leaf_smem, s));
         CK(cudaEventRecord(ev[2], s));
         Ctl hc;
         CK(cudaMemcpyAsync(&hc, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

@@ -171,6 +171,10 @@ struct KindOps {
     int deep_smem;            // dynamic shared memory of the on-chip deep stages
     const void *k_dbg_setup_partition, *k_dbg_counts, *k_dbg_pivot;
     const void *k_task_init, *k_task;   // task schedule
+    // leaf pass of the task graph for small inputs (items in one wave: more threads per
+    // item); the same kernel as k_leaf where no such variant exists
+    const void *k_leaf_small;
+    int leaf_small_block, leaf_small_smem;
     int task_block, task_tile;
 };
 

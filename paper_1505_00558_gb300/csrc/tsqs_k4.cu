@@ -44,6 +44,10 @@ KindOps make_ops() {
     o.k_deep_all = (const void *)k_deep_all<KIND>;
     o.deep_smem = (int)((kDeepTile + kDeepTile / kPadGroup<typename Key<KIND>::C>) * sizeof(typename Key<KIND>::C));
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 6>;
+    // small inputs (the task graph up to 2^20 keys): 256 threads x 16 keys per item
+    o.k_leaf_small = (const void *)k_leaf<KIND, 256, 16, 3>;
+    o.leaf_small_block = 256;
+    o.leaf_small_smem = o.leaf_smem;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;

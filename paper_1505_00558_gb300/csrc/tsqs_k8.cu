@@ -44,6 +44,9 @@ KindOps make_ops() {
     o.k_deep_all = (const void *)k_deep_all<KIND>;
     o.deep_smem = (int)((kDeepTile + kDeepTile / kPadGroup<typename Key<KIND>::C>) * sizeof(typename Key<KIND>::C));
     o.k_leaf = (const void *)k_leaf<KIND, kLeafBlock, kLeafMaxE, 3>;
+    o.k_leaf_small = o.k_leaf;
+    o.leaf_small_block = o.leaf_block;
+    o.leaf_small_smem = o.leaf_smem;
     o.k_pivot = (const void *)k_pivot<KIND>;
     o.k_finish = (const void *)k_level_end<KIND>;
     o.k_dbg_setup_partition = (const void *)k_dbg_setup_partition<KIND>;

@@ -267,3 +267,31 @@ def test_concurrent_task_sorts_on_four_streams(T, orc):
             assert t.cpu().numpy().tobytes() == _oracle(orc, a, 1)
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("kind_name", ["i32", "u32", "f32"])
+def test_small_input_leaf_every_item_size(T, orc, kind_name):
+    """Below 2^20 keys the task graph's leaf pass takes the small-input leaf kernel (256
+    threads x 16 keys per item): root segments of 1 .. 4096 keys in one call are all leaf
+    items of that kernel, each compared with the oracle."""
+    code, dt = KINDS[kind_name]
+    sizes = list(range(1, 4097, 9)) + [4095, 4096]
+    offs = np.zeros(len(sizes) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(sizes)
+    n = int(offs[-1])
+    assert n <= 1 << 20
+    a = _keys(kind_name, n, seed=77 + code)
+    exp = np.ascontiguousarray(a.copy())
+    orc.tsqs_sort_segments(exp, offs, code, threads=8)
+    ctx = T.Context()
+    t = _dev(a)
+    d_offs = torch.from_numpy(offs.astype(np.int64)).cuda()
+    T.sort_segmented_(t, d_offs, kind=code, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.status() == T.TSQS_OK
+    got = t.cpu().numpy().view(dt)
+    if got.tobytes() != exp.tobytes():
+        bad = [k for k in range(len(sizes))
+               if got[offs[k]:offs[k + 1]].tobytes() != exp[offs[k]:offs[k + 1]].tobytes()]
+        raise AssertionError(f"{len(bad)} items differ, sizes {[sizes[k] for k in bad[:5]]}")
+    ctx.close()
