@@ -22,7 +22,8 @@
 //     writes end-of-work rows for every block still polling (a launch that starts with
 //     none ends at once).
 // Keys of depth d are in buffer d % 2, as level d's are in the level-synchronous loop,
-// and the output of every step (leaf items, fills, deep items) is the same.
+// and every step hands on work of the same form (leaf items, fills, deep items), so the
+// leaf pass and the depth guard serve both schedules.
 #pragma once
 #include "tsqs_kernels.cuh"
 
