@@ -94,8 +94,9 @@ typedef struct {
 
 /* Per-context statistics of the last completed sort (filled by tsqs_ctx_stats). */
 typedef struct {
-    uint32_t levels;           /* partition levels run                                  */
-    uint32_t max_frontier;     /* most segments in one level                            */
+    uint32_t levels;           /* partition levels run (task-parallel schedule: depths
+                                  of the recursion reached)                             */
+    uint32_t max_frontier;     /* most segments in one level (0 task-parallel)          */
     uint64_t partition_keys;   /* keys read by all partition levels                     */
     uint64_t leaf_sorted_keys; /* keys finished by the on-chip sorter                   */
     uint64_t leaf_filled_keys; /* keys written by =p fills                              */
@@ -105,7 +106,7 @@ typedef struct {
     uint64_t deep_sorted_keys; /* keys sorted by the depth guard's bitonic fallback      */
     uint32_t level_keys_count; /* entries used in level_keys                            */
     uint32_t pad;
-    uint64_t level_keys[64];   /* keys partitioned at level i (first 64 levels)         */
+    uint64_t level_keys[64];   /* keys partitioned at level (or depth) i (first 64)     */
 } tsqs_stats;
 
 typedef struct tsqs_ctx tsqs_ctx;   /* scratch + captured graphs of one independent sorter */
