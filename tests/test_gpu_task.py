@@ -295,3 +295,43 @@ def test_small_input_leaf_every_item_size(T, orc, kind_name):
                if got[offs[k]:offs[k + 1]].tobytes() != exp[offs[k]:offs[k + 1]].tobytes()]
         raise AssertionError(f"{len(bad)} items differ, sizes {[sizes[k] for k in bad[:5]]}")
     ctx.close()
+
+
+@pytest.mark.parametrize("kind_name", list(KINDS))
+@pytest.mark.parametrize("n", [5000, 300_001])
+def test_task_schedule_unaligned_bases(T, orc, kind_name, n):
+    """Arrays whose base is aligned to the element but not to 16 bytes: the task kernel's
+    tiles start below the segment, the buffer's ends take scalar loads, and the =p fills
+    write a scalar head and tail around their 16-byte body."""
+    code, dt = KINDS[kind_name]
+    es = np.dtype(dt).itemsize
+    a = _keys(kind_name, n, seed=n % 97 + code)
+    a[::3] = a[2]                                   # long =p runs for the fills
+    exp = _oracle(orc, a, code)
+    ctx = _ctx(T, 2)
+    for off in range(1, 16 // es):
+        big = _dev(np.concatenate([a[:off], a, a[:4]]))   # room before and after
+        view = big[off:off + n]
+        assert view.data_ptr() % 16 != 0
+        T.sort_(view, kind=code, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.status() == T.TSQS_OK
+        assert view.cpu().numpy().tobytes() == exp
+        # the elements around the view are untouched
+        around = big.cpu().numpy()
+        assert around[:off].tobytes() == np.ascontiguousarray(a[:off]).view(around.dtype).tobytes()
+        assert around[off + n:].tobytes() == np.ascontiguousarray(a[:4]).view(around.dtype).tobytes()
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind_name", ["i32", "f64"])
+def test_task_schedule_host_array(T, orc, kind_name):
+    """A pinned host array sorted through tsqs_sort_host: below the size bound the task
+    schedule writes its =p fills and leaf sorts straight into the mapped host array."""
+    code, dt = KINDS[kind_name]
+    n = 700_001
+    a = _keys(kind_name, n, seed=31 + code)
+    exp = _oracle(orc, a, code)
+    h = torch.from_numpy(np.ascontiguousarray(a).view(np.int32 if np.dtype(dt).itemsize == 4 else np.int64).copy()).pin_memory()
+    assert T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, np.dtype(dt).itemsize, code, None) == 0
+    assert h.numpy().tobytes() == exp
