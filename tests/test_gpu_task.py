@@ -335,3 +335,32 @@ def test_task_schedule_host_array(T, orc, kind_name):
     h = torch.from_numpy(np.ascontiguousarray(a).view(np.int32 if np.dtype(dt).itemsize == 4 else np.int64).copy()).pin_memory()
     assert T.lib().tsqs_sort_host(ctypes.c_void_p(h.data_ptr()), n, np.dtype(dt).itemsize, code, None) == 0
     assert h.numpy().tobytes() == exp
+
+
+@pytest.mark.parametrize("kind_name", ["i64", "f64", "rec"])
+def test_depth_guard_in_task_schedule_wide_keys(T, orc, kind_name):
+    """The cooperative depth guard for 8-byte keys and records (the largest tile buffer):
+    with the guard at depth 2, most keys reach it, and the output equals the oracle's."""
+    n = 600_007
+    if kind_name == "rec":
+        a = records_u64(n, seed=17)
+        code = 7
+        t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    else:
+        code = KINDS[kind_name][0]
+        a = _keys(kind_name, n, seed=19 + code)
+        t = _dev(a)
+    exp = _oracle(orc, a, code)
+    L = T.lib()
+    L.tsqs_debug_set_deep_level(2)
+    try:
+        ctx = _ctx(T, 2)
+        T.sort_(t, kind=code, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.status() == T.TSQS_OK
+        st = ctx.stats()
+        ctx.close()
+    finally:
+        L.tsqs_debug_set_deep_level(0)
+    assert t.cpu().numpy().tobytes() == exp
+    assert st["deep_sorted_keys"] > n // 2
